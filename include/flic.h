@@ -1,0 +1,155 @@
+/*
+ * flic.h -- C ABI of the GB300 two-fluid FlIC/Godunov step library (libflic.so).
+ *
+ * The library advances a self-gravitating adiabatic gas and a collisionless
+ * "Boltzmann-moment" fluid (density, momentum, full symmetric energy and
+ * velocity-dispersion tensors) on a periodic uniform N^3 grid by the scheme of
+ * Kulikov 2013 (GPUPEGAS):
+ *   Sec. 2.3  Poisson equation for the total potential, Laplace(Phi) = 4 pi G (rho + n),
+ *             solved by FFT with the 27-point stencil symbol;
+ *   Sec. 2.1  gas Eulerian stage (face pressure/velocity from the linearised
+ *             Riemann solution), then the Lagrangian stage (face-flux transport);
+ *   Sec. 2.2  Boltzmann-moment Eulerian stage (closed-form face solution of the
+ *             6x6 linear system), then the Lagrangian stage;
+ *   Sec. 2.4  correctness checks kappa_gas, kappa_bme and the energy balance.
+ * Every stage runs in hand-written CUDA kernels for sm_103a; there is no CPU
+ * fallback.
+ *
+ * State layout (host arrays given to or taken from the library): 22 float64
+ * arrays of N^3 values each, structure of arrays, x fastest
+ * (index = i + N*(j + N*k)), in this field order:
+ *    0 rho   1 mx   2 my   3 mz   4 E (total gas energy density)   5 e (internal)
+ *    6 n     7 qx   8 qy   9 qz
+ *   10 nExx 11 nEyy 12 nEzz 13 nExy 14 nExz 15 nEyz   (n E_ij = Pi_ij + n u_i u_j)
+ *   16 Pxx  17 Pyy  18 Pzz  19 Pxy  20 Pxz  21 Pyz    (velocity-dispersion tensor)
+ * The grid covers [box_min, box_max]^3 with cell width h = (box_max - box_min)/N.
+ *
+ * Ownership: the library owns every device buffer it allocates (state, potential,
+ * FFT and reduction workspace).  Host pointers passed in are only read or written
+ * during the call.  "_device" entry points take device pointers owned by the
+ * caller and only read/write them during the call (stream-ordered).
+ *
+ * Errors: every call returns FLIC_OK (0) or a negative code; no exception or
+ * trap crosses the boundary.  flic_last_error() gives a message for the last
+ * failing call on a handle.
+ */
+#ifndef FLIC_H
+#define FLIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLIC_NFIELDS 22
+
+enum flic_status {
+    FLIC_OK = 0,
+    FLIC_ERR_INVALID_ARG = -1,   /* bad size, null pointer, unsupported option */
+    FLIC_ERR_CUDA = -2,          /* a CUDA runtime call failed (message in last_error) */
+    FLIC_ERR_NONPHYSICAL = -3,   /* step finished but produced rho, n, e or Pi_dd <= 0 or a non-finite value */
+    FLIC_ERR_TIMEOUT = -4,       /* a bounded device wait expired (reserved) */
+    FLIC_ERR_OOM = -5            /* device allocation failed */
+};
+
+enum flic_precision {
+    FLIC_FP64 = 0,   /* all storage and arithmetic in float64 */
+    FLIC_MIXED = 1   /* float32 storage and arithmetic; float64 for tau, diagnostics sums */
+};
+
+enum flic_poisson_bc {
+    FLIC_PERIODIC = 0,   /* periodic potential, 27-point symbol (Sec. 2.3) */
+    FLIC_ISOLATED = 1    /* zero-padded (2N)^3 convolution with -G h^3/|r| (reserved) */
+};
+
+typedef struct flic_grid_desc {
+    int n;               /* cells per axis (cube); N = 2^a 3^b, 8 <= N <= 1024 */
+    double box_min;      /* domain [box_min, box_max]^3 */
+    double box_max;
+    double gamma;        /* adiabatic index of the gas */
+    double G;            /* gravitational constant (0 disables gravity) */
+    double courant;      /* Courant number of the CFL step */
+    double eta;          /* energy-balance switch (1e-3) */
+    int precision;       /* enum flic_precision */
+    int poisson_bc;      /* enum flic_poisson_bc */
+} flic_grid_desc;
+
+/* Per-step record.  Conserved sums describe the state at the START of the step
+ * (with the potential solved in that step); kappa_* are measured on the
+ * post-Lagrangian state before the energy balance; vmax is the signal speed of
+ * the state at the END of the step (it sets the next CFL step). */
+typedef struct flic_diag {
+    double mass_gas, mass_bme;        /* sum rho h^3, sum n h^3 */
+    double mom[3];                    /* sum (m + q) h^3 */
+    double ekin_gas, eint_gas;        /* sum |m|^2/(2 rho) h^3, sum e h^3 */
+    double ekin_bme, etherm_bme;      /* sum |q|^2/(2 n) h^3, sum tr(Pi)/2 h^3 */
+    double epot;                      /* 1/2 sum (rho + n) Phi h^3 */
+    double kappa_gas, kappa_bme;      /* Sec. 2.4 integrals (h^3 sum of |.|) */
+    double vmax;                      /* max |v_d| + c_s, |u_d| + sqrt(3 Pi_dd / n) */
+    double dt;                        /* step size used */
+    double time;                      /* simulated time after the step */
+    long long step;                   /* steps taken */
+    int status;                       /* FLIC_OK or FLIC_ERR_NONPHYSICAL */
+} flic_diag;
+
+typedef struct flic_handle flic_handle;
+
+/* Allocates device state for one grid; *out receives the handle.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream) on which every launch of this
+ * handle is issued.  The state starts as zeros; call flic_set_state first. */
+int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out);
+
+/* Copies 22 host float64 arrays (field order above, N^3 each) to the device,
+ * converting to the storage precision on the device, and computes the initial
+ * signal speed.  Returns FLIC_ERR_NONPHYSICAL if the state has rho, n, e or
+ * Pi_dd <= 0 or a non-finite value (the state is still stored). */
+int flic_set_state(flic_handle* h, const double* const fields[FLIC_NFIELDS]);
+
+/* Same, from 22 device float64 arrays owned by the caller. */
+int flic_set_state_device(flic_handle* h, const double* const fields[FLIC_NFIELDS]);
+
+/* Copies the state to 22 host float64 arrays (N^3 each). */
+int flic_get_state(flic_handle* h, double* const fields[FLIC_NFIELDS]);
+
+/* Same, into 22 device float64 arrays owned by the caller. */
+int flic_get_state_device(flic_handle* h, double* const fields[FLIC_NFIELDS]);
+
+/* One full step (Poisson, tau, both fluids, kappa, energy balance, diagnostics).
+ * dt > 0: fixed step; dt <= 0: CFL step tau = courant * h / vmax computed on the
+ * device.  If dt_used is non-NULL the call waits for the step and stores tau;
+ * otherwise it returns after enqueueing (stream-ordered). */
+int flic_step(flic_handle* h, double dt, double* dt_used);
+
+/* nsteps consecutive steps with no host synchronisation (CUDA-graph replay after
+ * the first call for a given dt mode).  Waits for completion only if `sync`. */
+int flic_run(flic_handle* h, int nsteps, double dt, int sync);
+
+/* Solves Sec. 2.3 for the current state; phi_out (host, N^3 float64) may be NULL
+ * to keep the potential on the device only. */
+int flic_solve_poisson(flic_handle* h, double* phi_out);
+
+/* Record of the last completed step (waits for the stream). */
+int flic_step_diagnostics(flic_handle* h, flic_diag* out);
+
+/* Diagnostics of the CURRENT state (solves Poisson for E_pot; kappa of the
+ * current state; dt = 0). */
+int flic_diagnostics(flic_handle* h, flic_diag* out);
+
+/* Waits for all work of the handle. */
+int flic_sync(flic_handle* h);
+
+int flic_destroy(flic_handle* h);
+
+/* Message of the last failing call on h (or of the last failing flic_init_grid
+ * when h is NULL).  The pointer stays valid until the next call on h. */
+const char* flic_last_error(flic_handle* h);
+
+/* Library build information (compile flags, architecture). */
+const char* flic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLIC_H */

@@ -1,0 +1,37 @@
+// FFT Poisson solver interface (internal to libflic).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace flic {
+
+constexpr int FFT_MAX_RADIX = 16;
+
+// Radix sequence of one transform length (4s, then a 2, then 3s).
+struct FftPlan {
+    int nrad;
+    int radix[FFT_MAX_RADIX];
+};
+
+struct FftPlans {
+    FftPlan full;   // length N (y, z passes)
+    FftPlan half;   // length N/2 (packed real x pass)
+};
+
+int fft_plan_init(int N, FftPlans* p);
+
+// Sets the dynamic shared-memory limits of the FFT kernels for size N (call
+// once per size before launching or capturing).
+template <typename T>
+cudaError_t fft_prepare(int N);
+
+// Periodic solve of Sec. 2.3: phi = potential of s = rho + n.
+//   spec: (N/2+1) N N complex workspace; tw: table exp(-2 pi i j / tw_len),
+//   j < tw_len (tw_len a multiple of N); asin2[k] = 2/3 sin^2(pi k / N), k < N;
+//   coef_G_h2 = G h^2.
+template <typename T>
+cudaError_t poisson_periodic(const T* rho, const T* nd, T* phi, void* spec, int N, const FftPlans& pl,
+                             const void* tw, int tw_len, const T* asin2, double coef_G_h2,
+                             cudaStream_t st);
+
+}  // namespace flic

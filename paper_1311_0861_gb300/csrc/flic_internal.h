@@ -1,0 +1,49 @@
+// Declarations shared by the translation units of libflic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/flic.h"
+#include "flic_stencil.cuh"
+
+namespace flic {
+
+// Launch geometry of one fluid kernel: tiles of TX x TY columns, z chunks of tz planes.
+struct StepCfg {
+    int tx, ty;        // tile shape
+    int tiles_x, tiles_y;
+    int tz, blocks_z;
+    int threads;
+    size_t smem;
+    int num_blocks() const { return tiles_x * tiles_y * blocks_z; }
+};
+
+template <typename T> cudaError_t stencil_prepare();   // shared-memory limits, once
+template <typename T> StepCfg gas_cfg(int N, int tz);
+template <typename T> StepCfg bme_cfg(int N, int tz);
+template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
+template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
+
+// float64 <-> storage precision conversion of one field.
+template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);
+template <typename T> cudaError_t convert_out(const T* src, double* dst, size_t n, cudaStream_t st);
+
+// Conserved sums, kappa and signal speed of a whole state (partials[nb][Q_COUNT]).
+template <typename T>
+cudaError_t state_reduce(const T* state, size_t fs, const T* phi, size_t cells, double gamma,
+                         double* partials, int nb, double* vmax, unsigned int* status, cudaStream_t st);
+
+// Device scalars of a handle.
+enum Scalar { S_VMAX_CUR = 0, S_TAU, S_VMAX_NEXT, S_TIME, S_COUNT = 8 };
+
+// tau = dt (dt > 0) or courant*h / vmax_cur; clears vmax_next and the status word.
+cudaError_t step_prep(double* scal, unsigned int* status, double dt, double courant_h, cudaStream_t st);
+
+// Sums the per-block partials (fixed order, compensated), writes the record and
+// advances vmax_cur, time and the step counter.  count_step = 0 for a
+// diagnostics-only reduction.
+cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
+                          unsigned int* status, flic_diag* diag, int count_step, cudaStream_t st);
+
+}  // namespace flic

@@ -1,0 +1,544 @@
+// Fused FlIC/Godunov step of one fluid: Eulerian stage (face solutions, pressure /
+// stress and gravity sources), Lagrangian stage (upwind face fluxes), kappa check,
+// energy balance, CFL signal speed and conserved sums -- one kernel per fluid.
+//
+// Kulikov 2013 (GPUPEGAS): Sec. 2.1 (gas), Sec. 2.2 (Boltzmann moments),
+// Sec. 2.4 (kappa, energy balance).  Readings where the paper is silent:
+//   * Lagrangian flux F_{i+1/2} = W_{i+1/2} f_upwind with W the Eulerian face
+//     velocity of that face at time n (gas: V; moments: u_n*);
+//   * gravity by central differences of Phi^n with the time-n state;
+//   * after kappa is measured the dual variables are synchronised: gas takes
+//     e = E - |m|^2/(2 rho) when that is >= eta E, else resets E = e + |m|^2/(2 rho);
+//     moments take Pi = nE - q q^T/n when its trace is >= eta tr(nE) and its
+//     diagonal is positive, else reset nE = Pi + q q^T/n.
+//
+// Structure (2.5D z-march).  A block owns a TX x TY column tile and a chunk of
+// z planes.  It walks up the chunk with a two-plane ring of the input state in
+// shared memory over the tile plus a 2-cell halo (R2).  Per plane e:
+//   S0  load plane e+1 into the ring (conserved fields + 1/rho + Phi);
+//   S1  x- and y-face solutions of plane e over the tile plus a 1-cell halo (R1);
+//   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
+//   S3  upwind fluxes of f' for the tile cells; plane e-1 completes (its +z flux
+//       needs f'_e), gets the energy balance and is written out.
+// The transported state f' of the tile cell, its partial sum and the last z-flux
+// live in registers of the thread that owns the column.
+#pragma once
+
+#include "flic_common.cuh"
+
+namespace flic {
+
+template <typename T>
+struct StencilArgs {
+    const T* in;              // input state, field f at in + f * fs (fluid-local field order)
+    T* out;                   // output state, same layout
+    const T* phi;             // potential of the input state, N^3
+    size_t fs;                // field stride in elements
+    int n;                    // cells per axis
+    int tz;                   // z planes per block
+    int tiles_x;              // blocks along x (ceil(n / TX))
+    const double* tau;        // step size (device scalar)
+    double inv_h;             // 1 / h
+    T gamma, eta;
+    double* partials;         // [num_blocks][Q_COUNT] per-block sums (unscaled by h^3)
+    double* vmax;             // signal speed of the output state (atomic max)
+    unsigned int* status;     // ST_* bits
+};
+
+// ---------------------------------------------------------------------------
+// compensated accumulator: float pairs (two-sum) or plain double
+// ---------------------------------------------------------------------------
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {   // Knuth two-sum
+        float t = s + x;
+        float bb = t - s;
+        c += (s - (t - bb)) + (x - bb);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// ---------------------------------------------------------------------------
+// physics policies
+// ---------------------------------------------------------------------------
+// Ring layout: ring[slot][field][R2 cell].  Face layout: face[value][...].
+
+template <typename T>
+struct GasPhys {
+    static constexpr int NF = 6;      // rho, mx, my, mz, E, e
+    static constexpr int NR = 8;      // ring: conserved 6 + 1/rho + Phi
+    static constexpr int NFACE = 2;   // V, P
+    static constexpr int R_IRHO = 6, R_PHI = 7;
+    static constexpr int NQ = 8;      // accumulated quantities
+    static constexpr bool kR1Only(int) { return false; }
+
+    // Eulerian face solution (Sec. 2.1) between ring cells a (left) and b (right)
+    // along axis d.
+    static __device__ __forceinline__ void face(const T* ra, int a, const T* rb, int b, int R2,
+                                                int d, T gamma, T* outv) {
+        T rL = ra[0 * R2 + a], rR = rb[0 * R2 + b];
+        T vL = ra[(1 + d) * R2 + a] * ra[R_IRHO * R2 + a];
+        T vR = rb[(1 + d) * R2 + b] * rb[R_IRHO * R2 + b];
+        T pL = (gamma - T(1)) * ra[5 * R2 + a];
+        T pR = (gamma - T(1)) * rb[5 * R2 + b];
+        T z2 = rL * rR * gamma * (pL + pR) * rcp(rL + rR);   // squared acoustic impedance
+        T iz = rsq(z2);
+        T Z = z2 * iz;
+        outv[0] = T(0.5) * (vL + vR) + T(0.5) * (pL - pR) * iz;   // V
+        outv[1] = T(0.5) * (pL + pR) + T(0.5) * (vL - vR) * Z;    // P
+    }
+
+    // Eulerian update of one cell.  fm[d], fp[d]: face values on the -d and +d
+    // faces; g[d]: central-difference gradient of Phi.
+    static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
+                                                 const T fpv[3][NFACE], const T g[3], T tau,
+                                                 T rat, T gamma, T* f1) {
+        T rho = r[0 * R2 + c];
+        T m[3] = {r[1 * R2 + c], r[2 * R2 + c], r[3 * R2 + c]};
+        T E = r[4 * R2 + c], e = r[5 * R2 + c];
+        T dPV = T(0), dV = T(0), mg = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            dPV += fpv[d][1] * fpv[d][0] - fm[d][1] * fm[d][0];
+            dV += fpv[d][0] - fm[d][0];
+            mg += m[d] * g[d];
+        }
+        f1[0] = rho;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) f1[1 + d] = m[d] - rat * (fpv[d][1] - fm[d][1]) - tau * rho * g[d];
+        f1[4] = E - rat * dPV - tau * mg;
+        f1[5] = e - rat * (gamma - T(1)) * e * dV;
+    }
+
+    static __device__ __forceinline__ T normal_velocity(const T* facev, int) { return facev[0]; }
+
+    // Conserved sums of the time-n state (tile cells).
+    static __device__ __forceinline__ void accumulate_input(const T* r, int c, int R2, Acc<T>* q) {
+        T rho = r[0 * R2 + c], ir = r[R_IRHO * R2 + c];
+        T mx = r[1 * R2 + c], my = r[2 * R2 + c], mz = r[3 * R2 + c];
+        q[0].add(rho);
+        q[1].add(mx);
+        q[2].add(my);
+        q[3].add(mz);
+        q[4].add(T(0.5) * (mx * mx + my * my + mz * mz) * ir);
+        q[5].add(r[5 * R2 + c]);
+        q[6].add(T(0.5) * rho * r[R_PHI * R2 + c]);
+    }
+
+    // kappa, energy balance, signal speed and validity of an output cell.
+    static __device__ __forceinline__ void finish(T* f, T gamma, T eta, Acc<T>* q, T& vmax, bool& bad) {
+        T ir = rcp(f[0]);
+        T K = T(0.5) * (f[1] * f[1] + f[2] * f[2] + f[3] * f[3]) * ir;
+        T E = f[4], e = f[5];
+        q[7].add(fabs(E - e - K));
+        T epsE = E - K;
+        if (epsE >= eta * E) e = epsE; else E = e + K;
+        f[4] = E;
+        f[5] = e;
+        T cs = sqr_root(gamma * (gamma - T(1)) * e * ir);
+        T vm = fmax(fabs(f[1]), fmax(fabs(f[2]), fabs(f[3]))) * ir + cs;
+        vmax = fmax(vmax, vm);
+        bool ok = (f[0] > T(0)) && (e > T(0));
+#pragma unroll
+        for (int i = 0; i < NF; ++i) ok = ok && finite_val(f[i]);
+        bad = bad || !ok;
+    }
+
+    // Map of accumulated quantities to DiagQ slots.
+    static __device__ __forceinline__ int qslot(int i) {
+        const int s[NQ] = {Q_MASS_GAS, Q_MOMX, Q_MOMY, Q_MOMZ, Q_EKIN_GAS, Q_EINT_GAS, Q_EPOT, Q_KAPPA_GAS};
+        return s[i];
+    }
+};
+
+template <typename T>
+struct BmePhys {
+    // transported fields: n, qx, qy, qz, nExx, nEyy, nEzz, nExy, nExz, nEyz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz
+    static constexpr int NF = 16;
+    static constexpr int NR = 18;     // ring: the 16 + 1/n + Phi
+    static constexpr int NFACE = 6;   // u*_x, u*_y, u*_z, Pi*_xd, Pi*_yd, Pi*_zd
+    static constexpr int R_IN = 16, R_PHI = 17;
+    static constexpr int NQ = 8;
+    // energy-tensor fields are only needed on R1 (Eulerian update), not for faces
+    static constexpr bool kR1Only(int f) { return f >= 4 && f < 10; }
+
+    // index of tensor component (i, j) among (xx, yy, zz, xy, xz, yz)
+    static __device__ __forceinline__ int tc(int i, int j) {
+        return (i == j) ? i : (i + j + 2);   // (0,1)->3, (0,2)->4, (1,2)->5
+    }
+
+    // Eulerian face solution (Sec. 2.2), normal d with tangents t1 < t2.
+    static __device__ __forceinline__ void face(const T* ra, int a, const T* rb, int b, int R2,
+                                                int d, T, T* outv) {
+        const int t1 = (d == 0) ? 1 : 0;
+        const int t2 = (d == 2) ? 1 : 2;
+        T inL = ra[R_IN * R2 + a], inR = rb[R_IN * R2 + b];
+        T nL = ra[0 * R2 + a], nR = rb[0 * R2 + b];
+        T unL = ra[(1 + d) * R2 + a] * inL, unR = rb[(1 + d) * R2 + b] * inR;
+        T u1L = ra[(1 + t1) * R2 + a] * inL, u1R = rb[(1 + t1) * R2 + b] * inR;
+        T u2L = ra[(1 + t2) * R2 + a] * inL, u2R = rb[(1 + t2) * R2 + b] * inR;
+        const int pnn = 10 + tc(d, d), pn1 = 10 + tc(d, t1), pn2 = 10 + tc(d, t2);
+        T PnnL = ra[pnn * R2 + a], PnnR = rb[pnn * R2 + b];
+        T P1L = ra[pn1 * R2 + a], P1R = rb[pn1 * R2 + b];
+        T P2L = ra[pn2 * R2 + a], P2R = rb[pn2 * R2 + b];
+        const T s3 = T(1.7320508075688772935274463);
+        T rho = T(0.5) * (nL + nR);
+        T A = T(0.5) * (PnnL + PnnR);
+        T b1 = T(0.5) * (P1L + P1R);
+        T b2 = T(0.5) * (P2L + P2R);
+        T iz2 = rsq(rho * A);            // 1/sqrt(rho Pi_nn)
+        T Z2 = rho * A * iz2;            // sqrt(rho Pi_nn)
+        T Z1 = s3 * Z2;                  // sqrt(3 rho Pi_nn)
+        T iz1 = iz2 * (T(1) / s3);
+        T iA = rho * iz2 * iz2;          // 1 / Pi_nn
+        T dPnn = T(0.5) * (PnnL - PnnR);
+        T dun = T(0.5) * (unL - unR);
+        T cu = dPnn * (T(1) - s3) * iA * iz1;   // multiplies b_k in u_t
+        T cp = dun * rho * (s3 - T(1)) * iz2;   // multiplies b_k in Pi_nt
+        T un = T(0.5) * (unL + unR) + dPnn * iz1;
+        T u1 = T(0.5) * (u1L + u1R) + T(0.5) * (P1L - P1R) * iz2 + b1 * cu;
+        T u2 = T(0.5) * (u2L + u2R) + T(0.5) * (P2L - P2R) * iz2 + b2 * cu;
+        T Pnn = A + dun * Z1;
+        T P1 = b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp;
+        T P2 = b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp;
+        outv[d] = un;
+        outv[t1] = u1;
+        outv[t2] = u2;
+        outv[3 + d] = Pnn;
+        outv[3 + t1] = P1;
+        outv[3 + t2] = P2;
+    }
+
+    static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
+                                                 const T fpv[3][NFACE], const T g[3], T tau,
+                                                 T rat, T, T* f1) {
+        T n = r[0 * R2 + c];
+        T q[3] = {r[1 * R2 + c], r[2 * R2 + c], r[3 * R2 + c]};
+        T Pi[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Pi[k] = r[(10 + k) * R2 + c];
+        f1[0] = n;
+        // momentum: q_i -= r sum_d delta_d Pi*_{id} + tau n dPhi/dx_i
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s += fpv[d][3 + i] - fm[d][3 + i];
+            f1[1 + i] = q[i] - rat * s - tau * n * g[i];
+        }
+        // velocity jumps delta_d u*_i
+        T du[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) du[d][i] = fpv[d][i] - fm[d][i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int i = (k < 3) ? k : (k == 5 ? 1 : 0);
+            const int j = (k < 3) ? k : (k == 3 ? 1 : 2);
+            T sE = T(0), sP = T(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                sE += (fpv[d][3 + j] * fpv[d][i] + fpv[d][3 + i] * fpv[d][j])
+                    - (fm[d][3 + j] * fm[d][i] + fm[d][3 + i] * fm[d][j]);
+                sP += Pi[tc(j, d)] * du[d][i] + Pi[tc(i, d)] * du[d][j];
+            }
+            T nE = r[(4 + k) * R2 + c];
+            f1[4 + k] = nE - rat * sE - tau * (q[i] * g[j] + q[j] * g[i]);
+            f1[10 + k] = Pi[k] - rat * sP;
+        }
+    }
+
+    static __device__ __forceinline__ T normal_velocity(const T* facev, int d) { return facev[d]; }
+
+    static __device__ __forceinline__ void accumulate_input(const T* r, int c, int R2, Acc<T>* q) {
+        T n = r[0 * R2 + c], in = r[R_IN * R2 + c];
+        T qx = r[1 * R2 + c], qy = r[2 * R2 + c], qz = r[3 * R2 + c];
+        q[0].add(n);
+        q[1].add(qx);
+        q[2].add(qy);
+        q[3].add(qz);
+        q[4].add(T(0.5) * (qx * qx + qy * qy + qz * qz) * in);
+        q[5].add(T(0.5) * (r[10 * R2 + c] + r[11 * R2 + c] + r[12 * R2 + c]));
+        q[6].add(T(0.5) * n * r[R_PHI * R2 + c]);
+    }
+
+    static __device__ __forceinline__ void finish(T* f, T, T eta, Acc<T>* q, T& vmax, bool& bad) {
+        T in = rcp(f[0]);
+        T qq[6], PE[6];
+        T kap = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int i = (k < 3) ? k : (k == 5 ? 1 : 0);
+            const int j = (k < 3) ? k : (k == 3 ? 1 : 2);
+            qq[k] = f[1 + i] * f[1 + j] * in;
+            PE[k] = f[4 + k] - qq[k];
+            kap += fabs(PE[k] - f[10 + k]);
+        }
+        q[7].add(kap);
+        T trE = PE[0] + PE[1] + PE[2];
+        T trN = f[4] + f[5] + f[6];
+        bool take = (trE >= eta * trN) && (PE[0] > T(0)) && (PE[1] > T(0)) && (PE[2] > T(0));
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (take) f[10 + k] = PE[k]; else f[4 + k] = f[10 + k] + qq[k];
+        }
+        T vm = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            vm = fmax(vm, fabs(f[1 + d]) * in + sqr_root(T(3) * f[10 + d] * in));
+        vmax = fmax(vmax, vm);
+        bool ok = (f[0] > T(0)) && (f[10] > T(0)) && (f[11] > T(0)) && (f[12] > T(0));
+#pragma unroll
+        for (int i = 0; i < NF; ++i) ok = ok && finite_val(f[i]);
+        bad = bad || !ok;
+    }
+
+    static __device__ __forceinline__ int qslot(int i) {
+        const int s[NQ] = {Q_MASS_BME, Q_MOMX, Q_MOMY, Q_MOMZ, Q_EKIN_BME, Q_ETHERM_BME, Q_EPOT, Q_KAPPA_BME};
+        return s[i];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// shared-memory geometry of a tile
+// ---------------------------------------------------------------------------
+template <class P, typename T, int TX, int TY>
+struct Geom {
+    static constexpr int NT = TX * TY;
+    static constexpr int W2 = TX + 4, H2 = TY + 4, R2 = W2 * H2;   // tile + 2 halo
+    static constexpr int W1 = TX + 2, H1 = TY + 2, R1 = W1 * H1;   // tile + 1 halo
+    static constexpr int XFW = TX + 3;                               // x faces per R1 row
+    static constexpr int YFH = TY + 3;                               // y-face rows
+    static constexpr size_t ring_elems = size_t(2) * P::NR * R2;
+    static constexpr size_t xf_elems = size_t(P::NFACE) * H1 * XFW;
+    static constexpr size_t yf_elems = size_t(P::NFACE) * YFH * W1;
+    static constexpr size_t zc_elems = size_t(P::NFACE) * R1;
+    static constexpr size_t fp_elems = size_t(P::NF) * R1;
+    static constexpr size_t phim_elems = R1;
+    // the double-precision reduction scratch starts on a 16-byte boundary
+    static constexpr size_t red_offset =
+        ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems) * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t smem_bytes = red_offset + sizeof(double) * 32 * (P::NQ + 1);
+};
+
+// R1 cell i -> (jx, jy), tile cells first (so that i == threadIdx.x is the
+// thread's own column), then the one-cell border.
+template <int TX, int TY>
+__device__ __forceinline__ void r1_coords(int i, int& jx, int& jy) {
+    if (i < TX * TY) {
+        jx = 1 + i % TX;
+        jy = 1 + i / TX;
+        return;
+    }
+    int h = i - TX * TY;
+    if (h < TX + 2) { jx = h; jy = 0; return; }
+    h -= TX + 2;
+    if (h < TX + 2) { jx = h; jy = TY + 1; return; }
+    h -= TX + 2;
+    if (h < TY) { jx = 0; jy = 1 + h; return; }
+    h -= TY;
+    jx = TX + 1;
+    jy = 1 + h;
+}
+
+template <class P, typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+fluid_step_kernel(StencilArgs<T> a) {
+    using Gm = Geom<P, T, TX, TY>;
+    constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, R1 = Gm::R1, W1 = Gm::W1;
+    constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    T* xf = ring + Gm::ring_elems;
+    T* yf = xf + Gm::xf_elems;
+    T* zc = yf + Gm::yf_elems;
+    T* fpb = zc + Gm::zc_elems;
+    T* phim = fpb + Gm::fp_elems;
+    double* red = reinterpret_cast<double*>(smem_raw + Gm::red_offset);
+
+    const int tid = threadIdx.x;
+    const int N = a.n;
+    const size_t plane = size_t(N) * N;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % a.tiles_x) * TX;
+    const int y0 = (tile / a.tiles_x) * TY;
+    const int z0 = blockIdx.y * a.tz;
+    const int z1 = min(z0 + a.tz, N);
+    const T tau = T(*a.tau);
+    const T rat = T(*a.tau * a.inv_h);
+    const T half_ih = T(0.5 * a.inv_h);
+    const T gamma = a.gamma, eta = a.eta;
+
+    // own tile cell
+    const int own_tx = tid % TX, own_ty = tid / TX;
+    const bool own_valid = (x0 + own_tx < N) && (y0 + own_ty < N);
+    const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
+    const size_t own_g = size_t(wrap_mod(y0 + own_ty, N)) * N + wrap_mod(x0 + own_tx, N);
+
+    T fprev[NF], acc[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); }
+    T wz_prev = T(0);
+    Acc<T> q[P::NQ];
+    T vmax = T(0);
+    bool bad = false;
+
+    for (int p = z0 - 2; p <= z1 + 1; ++p) {
+        T* rp = ring + (p & 1) * NR * R2;        // plane p
+        T* re = ring + ((p - 1) & 1) * NR * R2;  // plane e = p - 1
+        const int e = p - 1;
+        // ---- S0: load plane p over R2 ------------------------------------
+        {
+            const size_t zoff = size_t(wrap_mod(p, N)) * plane;
+            for (int i = tid; i < R2; i += NT) {
+                const int ix = i % W2, iy = i / W2;
+                const bool r1 = (ix >= 1) && (ix <= TX + 2) && (iy >= 1) && (iy <= TY + 2);
+                const size_t g = zoff + size_t(wrap_mod(y0 + iy - 2, N)) * N + wrap_mod(x0 + ix - 2, N);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (P::kR1Only(f) && !r1) continue;
+                    rp[f * R2 + i] = a.in[f * a.fs + g];
+                }
+                rp[(NR - 2) * R2 + i] = rcp(rp[i]);
+                rp[(NR - 1) * R2 + i] = a.phi[g];
+            }
+        }
+        __syncthreads();
+        if (p < z0 - 1) continue;
+        const bool active = (p >= z0);
+        // ---- S1: x/y faces of plane e --------------------------------------
+        if (active) {
+            constexpr int NXF = Gm::H1 * Gm::XFW;
+            for (int i = tid; i < NXF; i += NT) {
+                const int fx = i % Gm::XFW, jy = i / Gm::XFW;
+                const int a2 = (jy + 1) * W2 + fx;
+                T v[NFACE];
+                P::face(re, a2, re, a2 + 1, R2, 0, gamma, v);
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
+            }
+            constexpr int NYF = Gm::YFH * W1;
+            for (int i = tid; i < NYF; i += NT) {
+                const int jx = i % W1, fy = i / W1;
+                const int a2 = fy * W2 + jx + 1;
+                T v[NFACE];
+                P::face(re, a2, re, a2 + W2, R2, 1, gamma, v);
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) yf[k * NYF + i] = v[k];
+            }
+        }
+        __syncthreads();
+        // ---- S2: z face e+1/2 and Eulerian update of plane e over R1 -------
+        for (int i = tid; i < R1; i += NT) {
+            int jx, jy;
+            r1_coords<TX, TY>(i, jx, jy);
+            const int c1 = jy * W1 + jx;
+            const int c2 = (jy + 1) * W2 + jx + 1;
+            T zn[NFACE];
+            P::face(re, c2, rp, c2, R2, 2, gamma, zn);
+            if (active) {
+                constexpr int NXF = Gm::H1 * Gm::XFW;
+                constexpr int NYF = Gm::YFH * W1;
+                T fm[3][NFACE], fpv[3][NFACE];
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) {
+                    fm[0][k] = xf[k * NXF + jy * Gm::XFW + jx];
+                    fpv[0][k] = xf[k * NXF + jy * Gm::XFW + jx + 1];
+                    fm[1][k] = yf[k * NYF + jy * W1 + jx];
+                    fpv[1][k] = yf[k * NYF + (jy + 1) * W1 + jx];
+                    fm[2][k] = zc[k * R1 + c1];
+                    fpv[2][k] = zn[k];
+                }
+                T g[3];
+                g[0] = (re[(NR - 1) * R2 + c2 + 1] - re[(NR - 1) * R2 + c2 - 1]) * half_ih;
+                g[1] = (re[(NR - 1) * R2 + c2 + W2] - re[(NR - 1) * R2 + c2 - W2]) * half_ih;
+                g[2] = (rp[(NR - 1) * R2 + c2] - phim[c1]) * half_ih;
+                T f1[NF];
+                P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, f1);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
+                if (i == tid) {
+                    // own tile cell: keep the -z face velocity for the Lagrangian stage
+                    wz_prev = P::normal_velocity(fm[2], 2);
+                    if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
+            phim[c1] = re[(NR - 1) * R2 + c2];
+        }
+        __syncthreads();
+        if (!active) continue;
+        // ---- S3: Lagrangian fluxes of the own tile cell --------------------
+        {
+            constexpr int NYF = Gm::YFH * W1;
+            const int cx = own_tx + 1, cy = own_ty + 1;
+            // face normal velocities W (gas: V stored first on every axis;
+            // moments: u*_d is value d of an axis-d face)
+            constexpr int KY = (NFACE == 2) ? 0 : 1;
+            const T Wxm = xf[cy * Gm::XFW + cx];
+            const T Wxp = xf[cy * Gm::XFW + cx + 1];
+            const T Wym = yf[KY * NYF + cy * W1 + cx];
+            const T Wyp = yf[KY * NYF + (cy + 1) * W1 + cx];
+            const T Wzm = wz_prev;
+            T out[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T* F = fpb + f * R1;
+                const T fc = F[own_c1];
+                const T Fxm = Wxm * (Wxm > T(0) ? F[own_c1 - 1] : fc);
+                const T Fxp = Wxp * (Wxp > T(0) ? fc : F[own_c1 + 1]);
+                const T Fym = Wym * (Wym > T(0) ? F[own_c1 - W1] : fc);
+                const T Fyp = Wyp * (Wyp > T(0) ? fc : F[own_c1 + W1]);
+                const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
+                out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
+                acc[f] = fc - rat * ((Fxp - Fxm) + (Fyp - Fym)) + rat * Fzm;
+                fprev[f] = fc;
+            }
+            const int l = e - 1;
+            if (l >= z0 && l < z1 && own_valid) {
+                P::finish(out, gamma, eta, q, vmax, bad);
+                const size_t g = size_t(l) * plane + own_g;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) a.out[f * a.fs + g] = out[f];
+            }
+        }
+    }
+
+    // ---- block reduction of the conserved sums, kappa and the signal speed ----
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int k = 0; k < P::NQ; ++k) {
+        double v = warp_sum(q[k].value());
+        if (lane == 0) red[warp * (P::NQ + 1) + k] = v;
+    }
+    double vm = warp_max((double)vmax);
+    unsigned int badw = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+    if (lane == 0) red[warp * (P::NQ + 1) + P::NQ] = vm;
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < P::NQ + 1; ++k) {
+            double v = (lane < NW) ? red[lane * (P::NQ + 1) + k] : 0.0;
+            if (k < P::NQ) {
+                v = warp_sum(v);
+                if (lane == 0) a.partials[(size_t(blockIdx.y) * gridDim.x + blockIdx.x) * Q_COUNT + P::qslot(k)] = v;
+            } else {
+                v = warp_max(v);
+                if (lane == 0) atomic_max_nonneg(a.vmax, v);
+            }
+        }
+    }
+    if (badw && lane == 0) atomicOr(a.status, ST_NONPHYSICAL);
+}
+
+}  // namespace flic

@@ -1,0 +1,186 @@
+// Conversion, whole-state reduction and per-step bookkeeping kernels of libflic.
+#include "flic_internal.h"
+
+namespace flic {
+
+template <typename T>
+__global__ void convert_in_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        dst[i] = T(src[i]);
+}
+template <typename T>
+__global__ void convert_out_kernel(const T* __restrict__ src, double* __restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        dst[i] = double(src[i]);
+}
+
+template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st) {
+    convert_in_kernel<T><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+template <typename T> cudaError_t convert_out(const T* src, double* dst, size_t n, cudaStream_t st) {
+    convert_out_kernel<T><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+template cudaError_t convert_in<float>(const double*, float*, size_t, cudaStream_t);
+template cudaError_t convert_in<double>(const double*, double*, size_t, cudaStream_t);
+template cudaError_t convert_out<float>(const float*, double*, size_t, cudaStream_t);
+template cudaError_t convert_out<double>(const double*, double*, size_t, cudaStream_t);
+
+// Conserved sums, kappa (Sec. 2.4) and signal speed of a whole state; one row of
+// Q_COUNT partial sums per block, plus an atomic max and the validity bit.
+template <typename T>
+__global__ void state_reduce_kernel(const T* __restrict__ s, size_t fs, const T* __restrict__ phi,
+                                    size_t cells, T gamma, double* partials, double* vmax,
+                                    unsigned int* status) {
+    __shared__ double red[32][Q_COUNT + 1];
+    Acc<T> q[Q_COUNT];
+    T vm = T(0);
+    bool bad = false;
+    for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < cells;
+         c += size_t(gridDim.x) * blockDim.x) {
+        T f[F_COUNT];
+#pragma unroll
+        for (int k = 0; k < F_COUNT; ++k) f[k] = s[k * fs + c];
+        const T ir = rcp(f[F_RHO]), in = rcp(f[F_N]);
+        const T K = T(0.5) * (f[F_MX] * f[F_MX] + f[F_MY] * f[F_MY] + f[F_MZ] * f[F_MZ]) * ir;
+        const T Kb = T(0.5) * (f[F_QX] * f[F_QX] + f[F_QY] * f[F_QY] + f[F_QZ] * f[F_QZ]) * in;
+        q[Q_MASS_GAS].add(f[F_RHO]);
+        q[Q_MASS_BME].add(f[F_N]);
+        q[Q_MOMX].add(f[F_MX] + f[F_QX]);
+        q[Q_MOMY].add(f[F_MY] + f[F_QY]);
+        q[Q_MOMZ].add(f[F_MZ] + f[F_QZ]);
+        q[Q_EKIN_GAS].add(K);
+        q[Q_EINT_GAS].add(f[F_EINT]);
+        q[Q_EKIN_BME].add(Kb);
+        q[Q_ETHERM_BME].add(T(0.5) * (f[F_PXX] + f[F_PYY] + f[F_PZZ]));
+        q[Q_EPOT].add(T(0.5) * (f[F_RHO] + f[F_N]) * phi[c]);
+        q[Q_KAPPA_GAS].add(fabs(f[F_E] - f[F_EINT] - K));
+        T kb = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int i = (k < 3) ? k : (k == 5 ? 1 : 0);
+            const int j = (k < 3) ? k : (k == 3 ? 1 : 2);
+            kb += fabs(f[F_NEXX + k] - f[F_PXX + k] - f[F_QX + i] * f[F_QX + j] * in);
+        }
+        q[Q_KAPPA_BME].add(kb);
+        const T cs = sqr_root(gamma * (gamma - T(1)) * f[F_EINT] * ir);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            vm = fmax(vm, fabs(f[F_MX + d]) * ir + cs);
+            vm = fmax(vm, fabs(f[F_QX + d]) * in + sqr_root(T(3) * f[F_PXX + d] * in));
+        }
+        bool ok = f[F_RHO] > T(0) && f[F_N] > T(0) && f[F_EINT] > T(0) && f[F_PXX] > T(0) &&
+                  f[F_PYY] > T(0) && f[F_PZZ] > T(0);
+#pragma unroll
+        for (int k = 0; k < F_COUNT; ++k) ok = ok && finite_val(f[k]);
+        bad = bad || !ok;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < Q_COUNT; ++k) {
+        double v = warp_sum(q[k].value());
+        if (lane == 0) red[warp][k] = v;
+    }
+    double m = warp_max((double)vm);
+    if (lane == 0) red[warp][Q_COUNT] = m;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONPHYSICAL);
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k <= Q_COUNT; ++k) {
+            double v = (lane < nw) ? red[lane][k] : 0.0;
+            if (k < Q_COUNT) {
+                v = warp_sum(v);
+                if (lane == 0) partials[size_t(blockIdx.x) * Q_COUNT + k] = v;
+            } else {
+                v = warp_max(v);
+                if (lane == 0) atomic_max_nonneg(vmax, v);
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t state_reduce(const T* state, size_t fs, const T* phi, size_t cells, double gamma,
+                         double* partials, int nb, double* vmax, unsigned int* status, cudaStream_t st) {
+    state_reduce_kernel<T><<<nb, 256, 0, st>>>(state, fs, phi, cells, T(gamma), partials, vmax, status);
+    return cudaGetLastError();
+}
+template cudaError_t state_reduce<float>(const float*, size_t, const float*, size_t, double, double*, int,
+                                         double*, unsigned int*, cudaStream_t);
+template cudaError_t state_reduce<double>(const double*, size_t, const double*, size_t, double, double*, int,
+                                          double*, unsigned int*, cudaStream_t);
+
+__global__ void step_prep_kernel(double* scal, unsigned int* status, double dt, double courant_h) {
+    const double v = scal[S_VMAX_CUR];
+    scal[S_TAU] = (dt > 0.0) ? dt : courant_h / v;
+    scal[S_VMAX_NEXT] = 0.0;
+    *status = 0u;
+}
+
+cudaError_t step_prep(double* scal, unsigned int* status, double dt, double courant_h, cudaStream_t st) {
+    step_prep_kernel<<<1, 1, 0, st>>>(scal, status, dt, courant_h);
+    return cudaGetLastError();
+}
+
+// One warp per quantity: lanes take blocks in a fixed stride (Neumaier sums),
+// then a fixed-order butterfly; the result does not depend on scheduling.
+__global__ void step_finalize_kernel(const double* __restrict__ pa, int na, const double* __restrict__ pb,
+                                     int nb, double h3, double* scal, unsigned int* status, flic_diag* d,
+                                     int count_step) {
+    __shared__ double res[Q_COUNT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < Q_COUNT; k += blockDim.x >> 5) {
+        double s = 0.0, c = 0.0;
+        for (int src = 0; src < 2; ++src) {
+            const double* p = src ? pb : pa;
+            const int n = src ? nb : na;
+            if (!p) continue;
+            for (int b = lane; b < n; b += 32) {
+                const double x = p[size_t(b) * Q_COUNT + k];
+                const double t = s + x;
+                c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+                s = t;
+            }
+        }
+        double v = s + c;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) res[k] = v * h3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d->mass_gas = res[Q_MASS_GAS];
+        d->mass_bme = res[Q_MASS_BME];
+        d->mom[0] = res[Q_MOMX];
+        d->mom[1] = res[Q_MOMY];
+        d->mom[2] = res[Q_MOMZ];
+        d->ekin_gas = res[Q_EKIN_GAS];
+        d->eint_gas = res[Q_EINT_GAS];
+        d->ekin_bme = res[Q_EKIN_BME];
+        d->etherm_bme = res[Q_ETHERM_BME];
+        d->epot = res[Q_EPOT];
+        d->kappa_gas = res[Q_KAPPA_GAS];
+        d->kappa_bme = res[Q_KAPPA_BME];
+        d->status = (*status & ST_NONPHYSICAL) ? FLIC_ERR_NONPHYSICAL : FLIC_OK;
+        if (count_step) {
+            d->vmax = scal[S_VMAX_NEXT];
+            d->dt = scal[S_TAU];
+            scal[S_TIME] += scal[S_TAU];
+            d->time = scal[S_TIME];
+            d->step += 1;
+            scal[S_VMAX_CUR] = scal[S_VMAX_NEXT];
+        } else {
+            d->vmax = scal[S_VMAX_NEXT];
+            d->dt = 0.0;
+            d->time = scal[S_TIME];
+        }
+    }
+}
+
+cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
+                          unsigned int* status, flic_diag* diag, int count_step, cudaStream_t st) {
+    step_finalize_kernel<<<1, 128, 0, st>>>(pa, na, pb, nb, h3, scal, status, diag, count_step);
+    return cudaGetLastError();
+}
+
+}  // namespace flic

@@ -1,0 +1,225 @@
+"""ctypes binding of libflic (include/flic.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; there is no Python or CPU
+fallback.  If libflic.so is missing or cannot be loaded, ``load()`` raises.
+Host arrays may be numpy float64 arrays or CPU torch tensors (pinned or not);
+CUDA torch tensors (float64) are passed to the device-pointer entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Mapping, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libflic.so")
+
+FIELDS = ("rho", "mx", "my", "mz", "E", "e",
+          "n", "qx", "qy", "qz",
+          "nExx", "nEyy", "nEzz", "nExy", "nExz", "nEyz",
+          "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz")
+NFIELDS = 22
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5
+FP64, MIXED = 0, 1
+PERIODIC, ISOLATED = 0, 1
+
+# every entry point declared in include/flic.h
+EXPORTS = ("flic_init_grid", "flic_set_state", "flic_set_state_device", "flic_get_state",
+           "flic_get_state_device", "flic_step", "flic_run", "flic_solve_poisson",
+           "flic_step_diagnostics", "flic_diagnostics", "flic_sync", "flic_destroy",
+           "flic_last_error", "flic_version")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("box_min", ctypes.c_double), ("box_max", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("G", ctypes.c_double), ("courant", ctypes.c_double),
+                ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("poisson_bc", ctypes.c_int)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("mass_gas", ctypes.c_double), ("mass_bme", ctypes.c_double),
+                ("mom", ctypes.c_double * 3), ("ekin_gas", ctypes.c_double),
+                ("eint_gas", ctypes.c_double), ("ekin_bme", ctypes.c_double),
+                ("etherm_bme", ctypes.c_double), ("epot", ctypes.c_double),
+                ("kappa_gas", ctypes.c_double), ("kappa_bme", ctypes.c_double),
+                ("vmax", ctypes.c_double), ("dt", ctypes.c_double), ("time", ctypes.c_double),
+                ("step", ctypes.c_longlong), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "mom"}
+        d["mom_x"], d["mom_y"], d["mom_z"] = self.mom[0], self.mom[1], self.mom[2]
+        d["nonphysical"] = self.status != OK
+        return d
+
+
+class FlicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libflic error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libflic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FlicError(ERR_INVALID_ARG, f"{path} not found: build it with paper_1311_0861_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.flic_init_grid.argtypes = [ctypes.POINTER(GridDesc), P, ctypes.POINTER(P)]
+    for name in ("flic_set_state", "flic_set_state_device", "flic_get_state", "flic_get_state_device"):
+        getattr(lib, name).argtypes = [P, ctypes.POINTER(P)]
+    lib.flic_step.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.flic_run.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.flic_solve_poisson.argtypes = [P, P]
+    lib.flic_step_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
+    lib.flic_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
+    lib.flic_sync.argtypes = [P]
+    lib.flic_destroy.argtypes = [P]
+    lib.flic_last_error.argtypes = [P]
+    lib.flic_last_error.restype = ctypes.c_char_p
+    lib.flic_version.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("flic_last_error", "flic_version"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr_of(a, want_device):
+    """(pointer, on_device) of a float64 array-like (numpy or torch)."""
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
+            raise FlicError(ERR_INVALID_ARG, "torch tensors must be contiguous float64")
+        return a.data_ptr(), a.is_cuda
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags.c_contiguous:
+        raise FlicError(ERR_INVALID_ARG, "numpy arrays must be C-contiguous float64")
+    return arr.ctypes.data, False
+
+
+def _field_list(state, n):
+    if isinstance(state, Mapping):
+        arrs = [state[f] for f in FIELDS]
+    else:
+        arrs = [state[i] for i in range(NFIELDS)]
+    for a in arrs:
+        if tuple(a.shape) != (n, n, n) and int(np.prod(a.shape)) != n ** 3:
+            raise FlicError(ERR_INVALID_ARG, f"field shape {tuple(a.shape)} != ({n},{n},{n})")
+    return arrs
+
+
+class Grid:
+    """One periodic N^3 grid of the two-fluid step (a libflic handle)."""
+
+    def __init__(self, n: int, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
+                 precision: str = "fp64", poisson: str = "periodic", stream: int = 0):
+        self.lib = load()
+        self.n = int(n)
+        self.h = (box[1] - box[0]) / n
+        d = GridDesc(int(n), box[0], box[1], gamma, G, courant, eta,
+                     {"fp64": FP64, "mixed": MIXED}[precision],
+                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson])
+        self._h = ctypes.c_void_p()
+        rc = self.lib.flic_init_grid(ctypes.byref(d), ctypes.c_void_p(stream or None), ctypes.byref(self._h))
+        if rc != OK:
+            raise FlicError(rc, self.lib.flic_last_error(None).decode())
+        self.precision = precision
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            raise FlicError(rc, self.lib.flic_last_error(self._h).decode())
+        return rc
+
+    def _ptrs(self, arrs):
+        ptrs, dev = [], None
+        for a in arrs:
+            p, is_dev = _ptr_of(a, None)
+            if dev is None:
+                dev = is_dev
+            elif dev != is_dev:
+                raise FlicError(ERR_INVALID_ARG, "mix of host and device arrays")
+            ptrs.append(p)
+        return (ctypes.c_void_p * NFIELDS)(*ptrs), dev
+
+    # -- ABI calls ---------------------------------------------------------------
+    def set_state(self, state, *, allow_nonphysical=False):
+        arrs = _field_list(state, self.n)
+        p, dev = self._ptrs(arrs)
+        fn = self.lib.flic_set_state_device if dev else self.lib.flic_set_state
+        rc = fn(self._h, p)
+        if rc == ERR_NONPHYSICAL and allow_nonphysical:
+            return rc
+        return self._check(rc)
+
+    def get_state(self, out=None):
+        """Returns a dict of float64 (N, N, N) numpy arrays, or fills ``out``
+        (dict or sequence of 22 host or device float64 arrays)."""
+        if out is None:
+            res = {f: np.empty((self.n, self.n, self.n)) for f in FIELDS}
+            p, _ = self._ptrs([res[f] for f in FIELDS])
+            self._check(self.lib.flic_get_state(self._h, p))
+            return res
+        arrs = _field_list(out, self.n)
+        p, dev = self._ptrs(arrs)
+        fn = self.lib.flic_get_state_device if dev else self.lib.flic_get_state
+        self._check(fn(self._h, p))
+        return out
+
+    def step(self, dt: float = 0.0, wait: bool = True):
+        if wait:
+            used = ctypes.c_double()
+            self._check(self.lib.flic_step(self._h, dt, ctypes.byref(used)))
+            return used.value
+        self._check(self.lib.flic_step(self._h, dt, None))
+        return None
+
+    def run(self, nsteps: int, dt: float = 0.0, sync: bool = True):
+        self._check(self.lib.flic_run(self._h, int(nsteps), dt, int(bool(sync))))
+
+    def solve_poisson(self, want=True):
+        if not want:
+            self._check(self.lib.flic_solve_poisson(self._h, None))
+            return None
+        phi = np.empty((self.n, self.n, self.n))
+        self._check(self.lib.flic_solve_poisson(self._h, ctypes.c_void_p(phi.ctypes.data)))
+        return phi
+
+    def step_diagnostics(self) -> dict:
+        d = Diag()
+        self._check(self.lib.flic_step_diagnostics(self._h, ctypes.byref(d)))
+        return d.as_dict()
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        self._check(self.lib.flic_diagnostics(self._h, ctypes.byref(d)))
+        return d.as_dict()
+
+    def sync(self):
+        self._check(self.lib.flic_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.flic_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

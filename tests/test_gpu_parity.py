@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 path: every field of one step within 1e-11 of the oracle (max abs error over
+the field's max abs), ten steps within 1e-10 relative L1 (sum |a-b| / sum |b|).
+Mixed path (float32 bulk): ten steps within 1e-4 relative L1 in density and
+1e-6 relative mass drift.  Sizes cover partial tiles (N not a multiple of the
+32 x 8 tile), several tiles with ragged z chunks, radix-3 FFT lengths, and the
+degenerate cases (uniform state, gravity off, fixed dt).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1311_0861_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = O.FIELDS
+
+
+@pytest.fixture(scope="module")
+def flic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_0861_gb300 import flic as F
+    import os
+    if not os.path.exists(F.LIB_PATH):
+        from paper_1311_0861_gb300 import build
+        build.build()
+    F.load()
+    return F
+
+
+def max_rel(a, b):
+    return {f: float(np.max(np.abs(a[f] - b[f])) / max(1e-300, np.max(np.abs(b[f])))) for f in FIELDS}
+
+
+def rel_l1(a, b):
+    return {f: float(np.sum(np.abs(a[f] - b[f])) / max(1e-300, np.sum(np.abs(b[f])))) for f in FIELDS}
+
+
+def run_gpu(F, setup, nsteps, precision="fp64", dt=0.0, G=1.0, graph=False):
+    with F.Grid(setup.shape[0], gamma=setup.gamma, G=G, precision=precision,
+                box=(-1.0, -1.0 + setup.h * setup.shape[0])) as g:
+        g.set_state(setup.state)
+        recs = []
+        if graph:
+            g.run(nsteps, dt)
+            recs.append(g.step_diagnostics())
+        else:
+            for _ in range(nsteps):
+                g.step(dt)
+                recs.append(g.step_diagnostics())
+        return g.get_state(), recs
+
+
+def run_oracle(setup, nsteps, dt=None, G=1.0):
+    prm = O.Params(h=setup.h, gamma=setup.gamma, G=G)
+    return O.run(setup.state, prm, nsteps, dt)
+
+
+@pytest.mark.parametrize("N", [8, 12, 24, 32, 48, 64])
+def test_poisson_fp64(flic, N):
+    s = I.random_state((N, N, N), seed=30 + N)
+    prm = O.Params(h=s.h)
+    ref = O.solve_poisson(s.state, prm)
+    with flic.Grid(N, precision="fp64", box=(-1.0, -1.0 + s.h * N)) as g:
+        g.set_state(s.state)
+        phi = g.solve_poisson()
+    assert np.max(np.abs(phi - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N", [16, 48, 96])
+def test_poisson_mixed(flic, N):
+    s = I.random_state((N, N, N), seed=40 + N)
+    prm = O.Params(h=s.h)
+    ref = O.solve_poisson(s.state, prm)
+    with flic.Grid(N, precision="mixed", box=(-1.0, -1.0 + s.h * N)) as g:
+        g.set_state(s.state)
+        phi = g.solve_poisson()
+    assert np.max(np.abs(phi - ref)) <= 2e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N,rough", [(8, True), (12, False), (24, True), (32, False), (48, True), (64, False)])
+def test_one_step_fp64(flic, N, rough):
+    s = I.random_state((N, N, N), seed=N, rough=rough)
+    ref, rrec = run_oracle(s, 1)
+    out, grec = run_gpu(flic, s, 1)
+    err = max_rel(out, ref)
+    assert max(err.values()) <= 1e-11, err
+    g, r = grec[-1], rrec[-1]
+    assert abs(g["dt"] - r["dt"]) <= 1e-14 * r["dt"]
+    for k in ("mass_gas", "mass_bme", "ekin_gas", "eint_gas", "ekin_bme", "etherm_bme", "epot",
+              "kappa_gas", "kappa_bme", "vmax"):
+        assert abs(g[k] - r[k]) <= 1e-11 * max(abs(r[k]), 1e-300), (k, g[k], r[k])
+    for a in "xyz":
+        scale = r["ekin_gas"] ** 0.5 + r["mass_gas"]
+        assert abs(g["mom_" + a] - r["mom_" + a]) <= 1e-12 * scale
+
+
+def test_sphere_ten_steps_fp64(flic):
+    """32^3 self-gravitating sphere, 10 CFL steps: relative L1 <= 1e-10 per field."""
+    s = I.sphere(32)
+    ref, rrec = run_oracle(s, 10)
+    out, grec = run_gpu(flic, s, 10)
+    err = rel_l1(out, ref)
+    assert max(err.values()) <= 1e-10, err
+    assert abs(grec[-1]["dt"] - rrec[-1]["dt"]) <= 1e-12 * rrec[-1]["dt"]
+
+
+def test_collision_ten_steps_fp64_graph(flic):
+    """32^3 two-galaxy collision through CUDA-graph replay."""
+    s = I.head_on(32)
+    ref, rrec = run_oracle(s, 10)
+    out, grec = run_gpu(flic, s, 10, graph=True)
+    err = rel_l1(out, ref)
+    assert max(err.values()) <= 1e-10, err
+    assert grec[-1]["step"] == 10
+
+
+def test_graph_replay_equals_single_steps(flic):
+    s = I.random_state((24, 24, 24), seed=5)
+    a, _ = run_gpu(flic, s, 4)
+    b, _ = run_gpu(flic, s, 4, graph=True)
+    for f in FIELDS:
+        assert np.array_equal(a[f], b[f]), f
+
+
+def test_mixed_ten_steps(flic):
+    """float32 bulk: 1e-4 relative L1 in density, 1e-6 relative mass drift."""
+    s = I.head_on(32)
+    ref, rrec = run_oracle(s, 10)
+    out, grec = run_gpu(flic, s, 10, precision="mixed")
+    err = rel_l1(out, ref)
+    assert err["rho"] <= 1e-4 and err["n"] <= 1e-4, err
+    with flic.Grid(32, precision="mixed") as g:
+        g.set_state(s.state)
+        m0 = g.diagnostics()
+        g.run(10)
+        m1 = g.diagnostics()
+    assert abs(m1["mass_gas"] - m0["mass_gas"]) <= 1e-6 * m0["mass_gas"]
+    assert abs(m1["mass_bme"] - m0["mass_bme"]) <= 1e-6 * m0["mass_bme"]
+
+
+def test_gravity_off_and_fixed_dt(flic):
+    s = I.random_state((16, 16, 16), seed=9, rough=True)
+    ref, _ = run_oracle(s, 2, dt=1e-3, G=0.0)
+    out, grec = run_gpu(flic, s, 2, dt=1e-3, G=0.0)
+    assert grec[-1]["dt"] == 1e-3
+    assert max(max_rel(out, ref).values()) <= 1e-11
+
+
+def test_uniform_state_fixed_point(flic):
+    N = 16
+    one = np.ones((N, N, N))
+    from helpers import state_from_primitives
+    P = {"xx": 0.5 * one, "yy": 0.7 * one, "zz": 0.6 * one, "xy": 0.1 * one, "xz": -0.05 * one, "yz": 0.02 * one}
+    st = state_from_primitives(1.3 * one, (0.2 * one, -0.1 * one, 0.05 * one), 0.8 * one, 0.9 * one,
+                               (-0.15 * one, 0.3 * one, 0.1 * one), P, 5.0 / 3.0)
+    s = I.Setup(st, 2.0 / N)
+    out, _ = run_gpu(flic, s, 3)
+    for f in FIELDS:
+        assert np.max(np.abs(out[f] - st[f])) <= 1e-14 * max(1.0, np.max(np.abs(st[f]))), f
+
+
+def test_state_round_trip_fp64(flic):
+    s = I.random_state((12, 12, 12), seed=2, rough=True)
+    with flic.Grid(12, precision="fp64") as g:
+        g.set_state(s.state)
+        out = g.get_state()
+    for f in FIELDS:
+        assert np.array_equal(out[f], s.state[f]), f
+
+
+def test_diagnostics_of_current_state(flic):
+    s = I.random_state((24, 24, 24), seed=3)
+    prm = O.Params(h=s.h)
+    phi = O.solve_poisson(s.state, prm)
+    ref = O.diagnostics(s.state, phi, prm)
+    with flic.Grid(24, precision="fp64", box=(-1.0, -1.0 + 24 * s.h)) as g:
+        g.set_state(s.state)
+        d = g.diagnostics()
+    for k, v in ref.items():
+        assert abs(d[k] - v) <= 1e-12 * max(1.0, abs(v)), (k, d[k], v)
+    assert abs(d["vmax"] - O.max_signal_speed(s.state, prm)) <= 1e-14
+
+
+def test_nonphysical_state_is_reported(flic):
+    s = I.random_state((8, 8, 8), seed=4)
+    st = dict(s.state)
+    st["rho"] = st["rho"].copy()
+    st["rho"][1, 2, 3] = -1.0
+    with flic.Grid(8) as g:
+        with pytest.raises(flic.FlicError) as ei:
+            g.set_state(st)
+        assert ei.value.code == flic.ERR_NONPHYSICAL
+
+
+def test_invalid_arguments(flic):
+    with pytest.raises(flic.FlicError) as ei:
+        flic.Grid(10)
+    assert ei.value.code == flic.ERR_INVALID_ARG
+    with pytest.raises(flic.FlicError):
+        flic.Grid(16, gamma=1.0)
