@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the full two-fluid FlIC/Godunov step on the 256^3 head-on
+two-galaxy collision (synthetic, seeded), through libflic's C ABI.
+
+One bench step = one full time step: FFT Poisson solve (Sec. 2.3), CFL step,
+gas and Boltzmann-moment Eulerian + Lagrangian stages, kappa, energy balance and
+diagnostics (Sec. 2.1-2.4).  The headline path is the float32-bulk ("mixed")
+path; the float64 path is measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas of the
+same workload (weak scaling; no data-path collective).  ``--impl reference``
+times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per full step at 256^3 (% HBM peak), mixed vs FP64, L1<=1e-4"
+UNIT = "cell-updates/s"
+# compulsory HBM bytes per cell of one launch: fields read (+ Phi) and written
+ALG_WORDS = {"gas": 7 + 6, "bme": 17 + 16, "poisson": 2 + 1}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-compare", action="store_true")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def aggregate(local: dict, world: int) -> dict:
+    """Max of the timed durations and sum of the cells over ranks (gloo, CPU)."""
+    if world == 1:
+        return {"max_s": local["seconds"], "cells": local["cells"]}
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local["seconds"]], dtype=torch.float64)
+    c = torch.tensor([float(local["cells"])], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return {"max_s": float(t.item()), "cells": float(c.item())}
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.marks = {}
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def mark(self, name):
+        self.marks[name] = time.perf_counter()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        t0, t1 = self.marks.get("t0", 0.0), self.marks.get("t1", 1e30)
+        inside = [s for t, s in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if len(inside) < 3:   # short timed region: widen to the warm-up + timed window
+            w0 = self.marks.get("w0", t0)
+            inside = [s for t, s in self.samples if w0 <= t <= t1]
+            window = "warm-up + timed region"
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in inside:
+            parts = [x.strip() for x in s.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(setup, budget_s: float):
+    """Times the FP64 oracle on a bounded slab of the workload.
+
+    The Poisson solve of the whole grid is timed once; the Eulerian/Lagrangian/
+    balance update is timed on a slab of S z-planes (S sized to ``budget_s``).
+    The full-step time is estimated as t_poisson + N * t_slab / S and the rate
+    as N^3 over that estimate."""
+    import oracle as O
+    st = setup.state
+    N = setup.shape[0]
+    prm = O.Params(h=setup.h, gamma=setup.gamma)
+    t = time.perf_counter()
+    phi = O.solve_poisson(st, prm)
+    t_poisson = time.perf_counter() - t
+    tau = O.cfl_dt(st, prm)
+    t = time.perf_counter()
+    O.advance_window(st, phi, tau, prm, zslab=(0, 1))
+    t_plane = time.perf_counter() - t
+    S = int(max(1, min(N, (budget_s - t_poisson) / max(t_plane, 1e-6))))
+    t = time.perf_counter()
+    O.advance_window(st, phi, tau, prm, zslab=(N // 2, N // 2 + S))
+    t_slab = time.perf_counter() - t
+    est = t_poisson + N * t_slab / S
+    return {"value": N ** 3 / est, "seconds_per_step_estimate": est, "planes": S,
+            "t_poisson": t_poisson, "t_slab": t_slab}
+
+
+def cpu_cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1311_0861_gb300 import inputs
+    setup = inputs.head_on(args.n)
+    # per-step budget so that warm-up + timed steps end within ~2 minutes
+    budget = max(0.5, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(setup, budget)
+    vals, secs, planes = [], [], []
+    for _ in range(args.steps):
+        r = oracle_sample(setup, budget)
+        vals.append(r["value"])
+        secs.append(r["seconds_per_step_estimate"])
+        planes.append(r["planes"])
+    value = float(np.median(vals))
+    cores = cpu_cores_used()
+    sample = (f"oracle (numpy FP64) on the {args.n}^3 head-on collision: whole-grid Poisson solve + "
+              f"update of a slab of {int(np.median(planes))} z-planes per step, scaled to the full grid")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"head-on two-galaxy collision {args.n}^3", "n": args.n,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_1311_0861_gb300 import flic, inputs
+    if not os.path.exists(flic.LIB_PATH):
+        from paper_1311_0861_gb300 import build
+        build.build()
+    N = args.n
+    setup = inputs.head_on(N) if rank == 0 else inputs.collision(N, seed=3 + 1000 * rank)
+    stream = torch.cuda.Stream()
+    esz = 4 if args.precision == "mixed" else 8
+    g = flic.Grid(N, precision=args.precision, gamma=setup.gamma, stream=stream.cuda_stream)
+    g.set_state(setup.state)
+    launches = g.launches_per_step()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.2)
+    clocks.mark("w0")
+    g.run(args.warmup, sync=True)
+    # ---- timed region: K steps, CUDA events per stage on the launching stream ----
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark("t0")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stage_ms, total_ms = g.profile(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    barrier(world)
+    clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    agg = aggregate({"seconds": elapsed_ms / 1e3, "cells": N ** 3 * args.steps}, world)
+    value = agg["cells"] / agg["max_s"]
+    d = g.step_diagnostics()
+
+    # roofline of the dominant kernel
+    kern = max(("gas", "bme"), key=lambda k: stage_ms[k])
+    avg_s = stage_ms[kern] / args.steps / 1e3
+    alg_bytes = ALG_WORDS[kern] * esz * N ** 3
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / avg_s / 1e9
+    roofline = {"bound": "hbm", "kernel": f"fluid_step_kernel<{'Bme' if kern == 'bme' else 'Gas'}Phys>",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3}
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            t = json.load(open(traffic_file)).get(f"{kern}-{args.precision}-{N}")
+            if t:
+                roofline["traffic"] = t
+        except Exception:
+            pass
+
+    # ---- end to end through the public API with pinned host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = torch.empty((22, N, N, N), dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty((22, N, N, N), dtype=torch.float64, pin_memory=True)
+        host_in.numpy()[...] = inputs.stack(setup.state)
+        ins = [host_in[i] for i in range(22)]
+        outs = [host_out[i] for i in range(22)]
+        barrier(world)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.set_state(ins)
+            g.step(wait=False)
+            g.get_state(outs)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t
+        aggE = aggregate({"seconds": e2e_s, "cells": N ** 3 * args.e2e_steps}, world)
+        e2e = {"value": aggE["cells"] / aggE["max_s"], "unit": UNIT,
+               "h2d_bytes_per_step": 22 * 8 * N ** 3, "d2h_bytes_per_step": 22 * 8 * N ** 3,
+               "steps": args.e2e_steps,
+               "what": "per step: set_state from pinned host float64 arrays, step, get_state to pinned host"}
+        del host_in, host_out
+
+    # ---- float64 path and mixed-vs-float64 accuracy on the same input ----
+    compare = None
+    if not args.no_compare and args.precision == "mixed":
+        g.set_state(setup.state)
+        g.run(10, sync=True)
+        mixed10 = g.get_state()
+        g.close()
+        g64 = flic.Grid(N, precision="fp64", gamma=setup.gamma, stream=stream.cuda_stream)
+        g64.set_state(setup.state)
+        g64.run(2, sync=True)
+        st64, tot64 = g64.profile(args.fp64_steps)
+        v64 = N ** 3 * args.fp64_steps / (tot64 / 1e3)
+        g64.set_state(setup.state)
+        g64.run(10, sync=True)
+        fp6410 = g64.get_state()
+        g64.close()
+        l1 = {f: float(np.sum(np.abs(mixed10[f] - fp6410[f])) / np.sum(np.abs(fp6410[f])))
+              for f in ("rho", "n", "E", "e", "Pxx")}
+        compare = {"fp64_value": v64 * world, "fp64_ms_per_step": tot64 / args.fp64_steps,
+                   "mixed_over_fp64": value / (v64 * world),
+                   "rel_l1_mixed_vs_fp64_after_10_steps": l1}
+    else:
+        g.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(setup, 20.0)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": (f"numpy FP64 oracle: whole-grid Poisson solve ({r['t_poisson']:.1f} s) + update of "
+                          f"{r['planes']} of {N} z-planes ({r['t_slab']:.1f} s), scaled to one full step")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": agg["max_s"] * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": f"head-on two-galaxy collision {N}^3 (seeded synthetic)",
+                           "n": N, "precision": args.precision, "poisson": "periodic FFT",
+                           "l2": f"inputs larger than L2 (state {22 * esz * N ** 3 / 2 ** 30:.2f} GiB)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * args.steps,
+                "clocks": clocks.summary(),
+                "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+                "compare": compare,
+                "status": "ok" if not d["nonphysical"] else "nonphysical"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

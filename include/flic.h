@@ -96,8 +96,10 @@ typedef struct flic_diag {
 typedef struct flic_handle flic_handle;
 
 /* Allocates device state for one grid; *out receives the handle.  `stream` is a
- * cudaStream_t (NULL = legacy default stream) on which every launch of this
- * handle is issued.  The state starts as zeros; call flic_set_state first. */
+ * cudaStream_t on which every launch of this handle is issued; NULL makes the
+ * library create (and later destroy) a non-blocking stream of its own.  The
+ * state starts as zeros; call flic_set_state first.  Errors: INVALID_ARG for an
+ * unsupported n or constants, OOM / CUDA on allocation failures (nothing leaks). */
 int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out);
 
 /* Copies 22 host float64 arrays (field order above, N^3 each) to the device,
@@ -124,6 +126,18 @@ int flic_step(flic_handle* h, double dt, double* dt_used);
 /* nsteps consecutive steps with no host synchronisation (CUDA-graph replay after
  * the first call for a given dt mode).  Waits for completion only if `sync`. */
 int flic_run(flic_handle* h, int nsteps, double dt, int sync);
+
+/* Profiling: runs nsteps steps as plain launches (no graph), recording CUDA
+ * events on the handle's stream around each stage; stage_ms[k] receives the
+ * summed device time of stage k over the steps and *total_ms (nullable) the
+ * elapsed time from the first to the last event.  Stages: 0 step setup and
+ * Poisson solve (Sec. 2.3), 1 gas kernel (Sec. 2.1, 2.4), 2 Boltzmann-moment
+ * kernel (Sec. 2.2, 2.4), 3 final reduction of the diagnostics. */
+#define FLIC_NSTAGES 4
+int flic_profile(flic_handle* h, int nsteps, double dt, double stage_ms[FLIC_NSTAGES], double* total_ms);
+
+/* Number of kernels one step launches (for launch accounting). */
+int flic_launches_per_step(flic_handle* h);
 
 /* Solves Sec. 2.3 for the current state; phi_out (host, N^3 float64) may be NULL
  * to keep the potential on the device only. */

@@ -76,12 +76,16 @@ static int enqueue_poisson(flic_handle* h) {
     return FLIC_OK;
 }
 
-// One full step on the handle's stream; flips the state buffers.
+// One full step on the handle's stream; flips the state buffers.  With `ev`
+// (5 events) the stage boundaries are recorded: start, after the Poisson solve,
+// after the gas kernel, after the moment kernel, after the final reduction.
 template <typename T>
-static int enqueue_step(flic_handle* h, double dt) {
+static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[0], h->st));
     FLIC_CK(h, step_prep(h->scal, h->status, dt, h->d.courant * h->h, h->st));
     int rc = enqueue_poisson<T>(h);
     if (rc) return rc;
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[1], h->st));
     StencilArgs<T> a;
     a.phi = reinterpret_cast<const T*>(h->phi);
     a.fs = h->fs;
@@ -99,6 +103,7 @@ static int enqueue_step(flic_handle* h, double dt) {
     a.tiles_x = h->gcfg.tiles_x;
     a.partials = h->part_gas;
     FLIC_CK(h, launch_gas<T>(a, h->gcfg, h->st));
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[2], h->st));
     // moments: fields 6..21
     a.in = field_ptr<T>(h->state[h->cur], h->fs, F_N);
     a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, F_N);
@@ -106,14 +111,16 @@ static int enqueue_step(flic_handle* h, double dt) {
     a.tiles_x = h->bcfg.tiles_x;
     a.partials = h->part_bme;
     FLIC_CK(h, launch_bme<T>(a, h->bcfg, h->st));
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));
     FLIC_CK(h, step_finalize(h->part_gas, h->gcfg.num_blocks(), h->part_bme, h->bcfg.num_blocks(),
                              h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->st));
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[4], h->st));
     h->cur = 1 - h->cur;
     return FLIC_OK;
 }
 
-static int do_step(flic_handle* h, double dt) {
-    return h->fp64 ? enqueue_step<double>(h, dt) : enqueue_step<float>(h, dt);
+static int do_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
+    return h->fp64 ? enqueue_step<double>(h, dt, ev) : enqueue_step<float>(h, dt, ev);
 }
 
 // signal speed and validity of the current state -> vmax_cur, status
@@ -347,6 +354,45 @@ int flic_run(flic_handle* h, int nsteps, double dt, int sync) {
         }
     }
     return FLIC_OK;
+}
+
+int flic_profile(flic_handle* h, int nsteps, double dt, double stage_ms[FLIC_NSTAGES], double* total_ms) {
+    if (!h || nsteps <= 0 || !stage_ms) return FLIC_ERR_INVALID_ARG;
+    const int ne = 5 * nsteps;
+    cudaEvent_t* ev = new cudaEvent_t[ne];
+    int made = 0, rc = FLIC_OK;
+    for (; made < ne; ++made) {
+        cudaError_t e = cudaEventCreate(&ev[made]);
+        if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rc = FLIC_ERR_CUDA; break; }
+    }
+    for (int s = 0; rc == FLIC_OK && s < nsteps; ++s) rc = do_step(h, dt, ev + 5 * s);
+    if (rc == FLIC_OK) {
+        cudaError_t e = cudaEventSynchronize(ev[ne - 1]);
+        if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rc = FLIC_ERR_CUDA; }
+    }
+    if (rc == FLIC_OK) {
+        for (int k = 0; k < FLIC_NSTAGES; ++k) stage_ms[k] = 0.0;
+        for (int s = 0; s < nsteps; ++s)
+            for (int k = 0; k < FLIC_NSTAGES; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[5 * s + k], ev[5 * s + k + 1]);
+                stage_ms[k] += ms;
+            }
+        if (total_ms) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[ne - 1]);
+            *total_ms = ms;
+        }
+    }
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    delete[] ev;
+    return rc;
+}
+
+int flic_launches_per_step(flic_handle* h) {
+    if (!h) return FLIC_ERR_INVALID_ARG;
+    // step setup, five FFT passes (none without gravity), two fluid kernels, final reduction
+    return 1 + (h->d.G != 0.0 ? 5 : 0) + 2 + 1;
 }
 
 int flic_solve_poisson(flic_handle* h, double* phi_out) {

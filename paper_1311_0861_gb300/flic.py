@@ -30,7 +30,9 @@ PERIODIC, ISOLATED = 0, 1
 EXPORTS = ("flic_init_grid", "flic_set_state", "flic_set_state_device", "flic_get_state",
            "flic_get_state_device", "flic_step", "flic_run", "flic_solve_poisson",
            "flic_step_diagnostics", "flic_diagnostics", "flic_sync", "flic_destroy",
-           "flic_last_error", "flic_version")
+           "flic_last_error", "flic_version", "flic_profile", "flic_launches_per_step")
+NSTAGES = 4
+STAGES = ("poisson", "gas", "bme", "finalize")
 
 
 class GridDesc(ctypes.Structure):
@@ -79,6 +81,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.flic_step.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.flic_run.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int]
     lib.flic_solve_poisson.argtypes = [P, P]
+    lib.flic_profile.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    lib.flic_launches_per_step.argtypes = [P]
     lib.flic_step_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
     lib.flic_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
     lib.flic_sync.argtypes = [P]
@@ -185,6 +190,22 @@ class Grid:
 
     def run(self, nsteps: int, dt: float = 0.0, sync: bool = True):
         self._check(self.lib.flic_run(self._h, int(nsteps), dt, int(bool(sync))))
+
+    def profile(self, nsteps: int, dt: float = 0.0):
+        """Per-stage device milliseconds summed over ``nsteps`` plain-launch steps,
+        and the total elapsed milliseconds."""
+        ms = (ctypes.c_double * NSTAGES)()
+        tot = ctypes.c_double()
+        self._check(self.lib.flic_profile(self._h, int(nsteps), dt, ms, ctypes.byref(tot)))
+        return dict(zip(STAGES, list(ms))), tot.value
+
+    def launches_per_step(self) -> int:
+        return self._check_count(self.lib.flic_launches_per_step(self._h))
+
+    def _check_count(self, rc):
+        if rc < 0:
+            raise FlicError(rc, self.lib.flic_last_error(self._h).decode())
+        return rc
 
     def solve_poisson(self, want=True):
         if not want:
