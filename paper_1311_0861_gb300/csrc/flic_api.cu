@@ -32,6 +32,7 @@ struct flic_handle {
     double* part_gas = nullptr;
     double* part_bme = nullptr;
     double* part_diag = nullptr;
+    double* level1 = nullptr;         // second-level partial sums
     int nb_diag = 0;
     StepCfg gcfg, bcfg;
     flic_diag* diag_dev = nullptr;    // [0] last step, [1] current-state diagnostics
@@ -113,7 +114,7 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
     FLIC_CK(h, launch_bme<T>(a, h->bcfg, h->st));
     if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));
     FLIC_CK(h, step_finalize(h->part_gas, h->gcfg.num_blocks(), h->part_bme, h->bcfg.num_blocks(),
-                             h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->st));
+                             h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
     if (ev) FLIC_CK(h, cudaEventRecord(ev[4], h->st));
     h->cur = 1 - h->cur;
     return FLIC_OK;
@@ -185,7 +186,7 @@ static void free_all(flic_handle* h) {
         if (h->state[i]) cudaFree(h->state[i]);
     }
     void* bufs[] = {h->phi, h->spec, h->tw, h->asin2, h->scal, h->status, h->part_gas, h->part_bme,
-                    h->part_diag, h->diag_dev, h->staging};
+                    h->part_diag, h->level1, h->diag_dev, h->staging};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->diag_host) cudaFreeHost(h->diag_host);
@@ -242,6 +243,7 @@ static int init_impl(flic_handle* h) {
     FLIC_CK(h, cudaMalloc(&h->part_gas, pg * sizeof(double)));
     FLIC_CK(h, cudaMalloc(&h->part_bme, pb * sizeof(double)));
     FLIC_CK(h, cudaMalloc(&h->part_diag, size_t(h->nb_diag) * Q_COUNT * sizeof(double)));
+    FLIC_CK(h, cudaMalloc(&h->level1, size_t(FINALIZE_ROWS) * Q_COUNT * sizeof(double)));
     FLIC_CK(h, cudaMemsetAsync(h->part_gas, 0, pg * sizeof(double), h->st));
     FLIC_CK(h, cudaMemsetAsync(h->part_bme, 0, pb * sizeof(double), h->st));
     FLIC_CK(h, cudaMalloc(&h->diag_dev, 2 * sizeof(flic_diag)));
@@ -391,8 +393,8 @@ int flic_profile(flic_handle* h, int nsteps, double dt, double stage_ms[FLIC_NST
 
 int flic_launches_per_step(flic_handle* h) {
     if (!h) return FLIC_ERR_INVALID_ARG;
-    // step setup, five FFT passes (none without gravity), two fluid kernels, final reduction
-    return 1 + (h->d.G != 0.0 ? 5 : 0) + 2 + 1;
+    // step setup, five FFT passes (none without gravity), two fluid kernels, two-level reduction
+    return 1 + (h->d.G != 0.0 ? 5 : 0) + 2 + 2;
 }
 
 int flic_solve_poisson(flic_handle* h, double* phi_out) {
@@ -427,7 +429,7 @@ int flic_diagnostics(flic_handle* h, flic_diag* out) {
                  : enqueue_state_check<float>(h, h->scal + S_VMAX_NEXT);
     if (rc) return rc;
     FLIC_CK(h, step_finalize(h->part_diag, h->nb_diag, nullptr, 0, h->h * h->h * h->h, h->scal, h->status,
-                             h->diag_dev + 1, 0, h->st));
+                             h->diag_dev + 1, 0, h->level1, h->st));
     FLIC_CK(h, cudaMemcpyAsync(h->diag_host, h->diag_dev, 2 * sizeof(flic_diag), cudaMemcpyDeviceToHost, h->st));
     FLIC_CK(h, cudaStreamSynchronize(h->st));
     *out = h->diag_host[1];

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
-#include "../../include/flic.h"
+#include "flic.h"
 #include "flic_stencil.cuh"
 
 namespace flic {
@@ -42,8 +42,10 @@ cudaError_t step_prep(double* scal, unsigned int* status, double dt, double cour
 
 // Sums the per-block partials (fixed order, compensated), writes the record and
 // advances vmax_cur, time and the step counter.  count_step = 0 for a
-// diagnostics-only reduction.
+// diagnostics-only reduction.  level1: FINALIZE_ROWS x Q_COUNT doubles of scratch.
+constexpr int FINALIZE_ROWS = 64;
 cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
-                          unsigned int* status, flic_diag* diag, int count_step, cudaStream_t st);
+                          unsigned int* status, flic_diag* diag, int count_step, double* level1,
+                          cudaStream_t st);
 
 }  // namespace flic

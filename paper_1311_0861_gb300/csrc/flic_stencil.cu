@@ -6,13 +6,14 @@ namespace flic {
 namespace {
 
 template <typename T> struct Tiles;
-// float32: 32 x 8 columns for both fluids; float64: the moment kernel's shared
-// memory needs a 32 x 4 tile.
+// 32 x 8 column tiles; minimum resident blocks per SM for the register budget
+// (float32: 3 gas / 2 moment blocks; float64: 2 gas / 1 moment block, whose
+// shared memory takes most of the SM).
 template <> struct Tiles<float> {
-    static constexpr int GX = 32, GY = 8, BX = 32, BY = 8;
+    static constexpr int GX = 32, GY = 8, GB = 3, BX = 32, BY = 8, BB = 2;
 };
 template <> struct Tiles<double> {
-    static constexpr int GX = 32, GY = 8, BX = 32, BY = 4;
+    static constexpr int GX = 32, GY = 8, GB = 2, BX = 32, BY = 8, BB = 1;
 };
 
 template <class P, typename T, int TX, int TY>
@@ -37,15 +38,15 @@ StepCfg make_cfg(int N, int tz) {
     return c;
 }
 
-template <class P, typename T, int TX, int TY>
+template <class P, typename T, int TX, int TY, int MB>
 cudaError_t prepare() {
-    return cudaFuncSetAttribute(fluid_step_kernel<P, T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(fluid_step_kernel<P, T, TX, TY, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geom<P, T, TX, TY>::smem_bytes);
 }
 
-template <class P, typename T, int TX, int TY>
+template <class P, typename T, int TX, int TY, int MB>
 cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-    fluid_step_kernel<P, T, TX, TY><<<dim3(c.tiles_x * c.tiles_y, c.blocks_z), c.threads, c.smem, st>>>(a);
+    fluid_step_kernel<P, T, TX, TY, MB><<<dim3(c.tiles_x * c.tiles_y, c.blocks_z), c.threads, c.smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -58,16 +59,16 @@ template <typename T> StepCfg bme_cfg(int N, int tz) {
     return make_cfg<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY>(N, tz);
 }
 template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-    return launch<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY>(a, c, st);
+    return launch<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB>(a, c, st);
 }
 template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-    return launch<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY>(a, c, st);
+    return launch<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB>(a, c, st);
 }
 
 template <typename T> cudaError_t stencil_prepare() {
-    cudaError_t e = prepare<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY>();
+    cudaError_t e = prepare<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB>();
     if (e != cudaSuccess) return e;
-    return prepare<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY>();
+    return prepare<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB>();
 }
 template cudaError_t stencil_prepare<float>();
 template cudaError_t stencil_prepare<double>();

@@ -15,7 +15,9 @@
 // Structure (2.5D z-march).  A block owns a TX x TY column tile and a chunk of
 // z planes.  It walks up the chunk with a two-plane ring of the input state in
 // shared memory over the tile plus a 2-cell halo (R2).  Per plane e:
-//   S0  load plane e+1 into the ring (conserved fields + 1/rho + Phi);
+//   S0  asynchronous copy of plane e+1 into the ring (conserved fields + Phi;
+//       1/rho is filled in when the copy has landed), issued as soon as the
+//       slot's previous plane has been consumed so that it overlaps S3;
 //   S1  x- and y-face solutions of plane e over the tile plus a 1-cell halo (R1);
 //   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
 //   S3  upwind fluxes of f' for the tile cells; plane e-1 completes (its +z flux
@@ -323,10 +325,12 @@ struct Geom {
     static constexpr size_t zc_elems = size_t(P::NFACE) * R1;
     static constexpr size_t fp_elems = size_t(P::NF) * R1;
     static constexpr size_t phim_elems = R1;
-    // the double-precision reduction scratch starts on a 16-byte boundary
+    // the double-precision reduction scratch starts on a 16-byte boundary,
+    // followed by the wrapped-coordinate tables (W2 + H2 ints)
     static constexpr size_t red_offset =
         ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems) * sizeof(T) + 15) / 16 * 16;
-    static constexpr size_t smem_bytes = red_offset + sizeof(double) * 32 * (P::NQ + 1);
+    static constexpr size_t tab_offset = red_offset + sizeof(double) * 32 * (P::NQ + 1);
+    static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (W2 + H2);
 };
 
 // R1 cell i -> (jx, jy), tile cells first (so that i == threadIdx.x is the
@@ -349,12 +353,25 @@ __device__ __forceinline__ void r1_coords(int i, int& jx, int& jy) {
     jy = 1 + h;
 }
 
-template <class P, typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+// Asynchronous 4- or 8-byte global -> shared copy (no register staging).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class P, typename T, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
 fluid_step_kernel(StencilArgs<T> a) {
     using Gm = Geom<P, T, TX, TY>;
-    constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, R1 = Gm::R1, W1 = Gm::W1;
+    constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, H2 = Gm::H2, R1 = Gm::R1, W1 = Gm::W1;
     constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE;
+    constexpr int NXF = Gm::H1 * Gm::XFW;
+    constexpr int NYF = Gm::YFH * W1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);
     T* xf = ring + Gm::ring_elems;
@@ -363,6 +380,8 @@ fluid_step_kernel(StencilArgs<T> a) {
     T* fpb = zc + Gm::zc_elems;
     T* phim = fpb + Gm::fp_elems;
     double* red = reinterpret_cast<double*>(smem_raw + Gm::red_offset);
+    int* xoff = reinterpret_cast<int*>(smem_raw + Gm::tab_offset);   // wrapped x of R2 columns
+    int* yoff = xoff + W2;                                             // wrapped y * N of R2 rows
 
     const int tid = threadIdx.x;
     const int N = a.n;
@@ -377,46 +396,53 @@ fluid_step_kernel(StencilArgs<T> a) {
     const T half_ih = T(0.5 * a.inv_h);
     const T gamma = a.gamma, eta = a.eta;
 
+    for (int i = tid; i < W2; i += NT) xoff[i] = wrap_mod(x0 + i - 2, N);
+    for (int i = tid; i < H2; i += NT) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
+    __syncthreads();
+
     // own tile cell
     const int own_tx = tid % TX, own_ty = tid / TX;
     const bool own_valid = (x0 + own_tx < N) && (y0 + own_ty < N);
     const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
-    const size_t own_g = size_t(wrap_mod(y0 + own_ty, N)) * N + wrap_mod(x0 + own_tx, N);
+    const size_t own_g = size_t(yoff[own_ty + 2]) + xoff[own_tx + 2];
 
-    T fprev[NF], acc[NF];
+    // S0 of plane pz: asynchronous copies into ring slot pz & 1 (conserved
+    // fields and Phi; 1/rho is filled in after the copies land).
+    auto issue_plane = [&](int pz) {
+        T* dst = ring + (pz & 1) * NR * R2;
+        const size_t zoff = size_t(wrap_mod(pz, N)) * plane;
+        for (int i = tid; i < R2; i += NT) {
+            const int ix = i % W2, iy = i / W2;
+            const bool r1 = (ix >= 1) && (ix <= TX + 2) && (iy >= 1) && (iy <= TY + 2);
+            const size_t g = zoff + size_t(yoff[iy]) + xoff[ix];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); }
+            for (int f = 0; f < NF; ++f) {
+                if (P::kR1Only(f) && !r1) continue;
+                cp_async_elem(dst + f * R2 + i, a.in + f * a.fs + g);
+            }
+            cp_async_elem(dst + (NR - 1) * R2 + i, a.phi + g);
+        }
+    };
+
+    T fprev[NF], acc[NF], fown[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); fown[f] = T(0); }
     T wz_prev = T(0);
     Acc<T> q[P::NQ];
     T vmax = T(0);
     bool bad = false;
 
+    issue_plane(z0 - 2);
     for (int p = z0 - 2; p <= z1 + 1; ++p) {
         T* rp = ring + (p & 1) * NR * R2;        // plane p
         T* re = ring + ((p - 1) & 1) * NR * R2;  // plane e = p - 1
         const int e = p - 1;
-        // ---- S0: load plane p over R2 ------------------------------------
-        {
-            const size_t zoff = size_t(wrap_mod(p, N)) * plane;
-            for (int i = tid; i < R2; i += NT) {
-                const int ix = i % W2, iy = i / W2;
-                const bool r1 = (ix >= 1) && (ix <= TX + 2) && (iy >= 1) && (iy <= TY + 2);
-                const size_t g = zoff + size_t(wrap_mod(y0 + iy - 2, N)) * N + wrap_mod(x0 + ix - 2, N);
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (P::kR1Only(f) && !r1) continue;
-                    rp[f * R2 + i] = a.in[f * a.fs + g];
-                }
-                rp[(NR - 2) * R2 + i] = rcp(rp[i]);
-                rp[(NR - 1) * R2 + i] = a.phi[g];
-            }
-        }
-        __syncthreads();
-        if (p < z0 - 1) continue;
         const bool active = (p >= z0);
-        // ---- S1: x/y faces of plane e --------------------------------------
+        cp_async_wait_all();
+        __syncthreads();
+        // ---- 1/rho of plane p; S1: x/y faces of plane e ----------------------
+        for (int i = tid; i < R2; i += NT) rp[(NR - 2) * R2 + i] = rcp(rp[i]);
         if (active) {
-            constexpr int NXF = Gm::H1 * Gm::XFW;
             for (int i = tid; i < NXF; i += NT) {
                 const int fx = i % Gm::XFW, jy = i / Gm::XFW;
                 const int a2 = (jy + 1) * W2 + fx;
@@ -425,7 +451,6 @@ fluid_step_kernel(StencilArgs<T> a) {
 #pragma unroll
                 for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
             }
-            constexpr int NYF = Gm::YFH * W1;
             for (int i = tid; i < NYF; i += NT) {
                 const int jx = i % W1, fy = i / W1;
                 const int a2 = fy * W2 + jx + 1;
@@ -436,50 +461,53 @@ fluid_step_kernel(StencilArgs<T> a) {
             }
         }
         __syncthreads();
-        // ---- S2: z face e+1/2 and Eulerian update of plane e over R1 -------
-        for (int i = tid; i < R1; i += NT) {
-            int jx, jy;
-            r1_coords<TX, TY>(i, jx, jy);
-            const int c1 = jy * W1 + jx;
-            const int c2 = (jy + 1) * W2 + jx + 1;
-            T zn[NFACE];
-            P::face(re, c2, rp, c2, R2, 2, gamma, zn);
-            if (active) {
-                constexpr int NXF = Gm::H1 * Gm::XFW;
-                constexpr int NYF = Gm::YFH * W1;
-                T fm[3][NFACE], fpv[3][NFACE];
+        // ---- S2: z face e+1/2 and Eulerian update of plane e over R1 ---------
+        if (p >= z0 - 1) {
+            for (int i = tid; i < R1; i += NT) {
+                int jx, jy;
+                r1_coords<TX, TY>(i, jx, jy);
+                const int c1 = jy * W1 + jx;
+                const int c2 = (jy + 1) * W2 + jx + 1;
+                T zn[NFACE];
+                P::face(re, c2, rp, c2, R2, 2, gamma, zn);
+                if (active) {
+                    T fm[3][NFACE], fpv[3][NFACE];
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) {
-                    fm[0][k] = xf[k * NXF + jy * Gm::XFW + jx];
-                    fpv[0][k] = xf[k * NXF + jy * Gm::XFW + jx + 1];
-                    fm[1][k] = yf[k * NYF + jy * W1 + jx];
-                    fpv[1][k] = yf[k * NYF + (jy + 1) * W1 + jx];
-                    fm[2][k] = zc[k * R1 + c1];
-                    fpv[2][k] = zn[k];
-                }
-                T g[3];
-                g[0] = (re[(NR - 1) * R2 + c2 + 1] - re[(NR - 1) * R2 + c2 - 1]) * half_ih;
-                g[1] = (re[(NR - 1) * R2 + c2 + W2] - re[(NR - 1) * R2 + c2 - W2]) * half_ih;
-                g[2] = (rp[(NR - 1) * R2 + c2] - phim[c1]) * half_ih;
-                T f1[NF];
-                P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, f1);
+                    for (int k = 0; k < NFACE; ++k) {
+                        fm[0][k] = xf[k * NXF + jy * Gm::XFW + jx];
+                        fpv[0][k] = xf[k * NXF + jy * Gm::XFW + jx + 1];
+                        fm[1][k] = yf[k * NYF + jy * W1 + jx];
+                        fpv[1][k] = yf[k * NYF + (jy + 1) * W1 + jx];
+                        fm[2][k] = zc[k * R1 + c1];
+                        fpv[2][k] = zn[k];
+                    }
+                    T g[3];
+                    g[0] = (re[(NR - 1) * R2 + c2 + 1] - re[(NR - 1) * R2 + c2 - 1]) * half_ih;
+                    g[1] = (re[(NR - 1) * R2 + c2 + W2] - re[(NR - 1) * R2 + c2 - W2]) * half_ih;
+                    g[2] = (rp[(NR - 1) * R2 + c2] - phim[c1]) * half_ih;
+                    T f1[NF];
+                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, f1);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
-                if (i == tid) {
-                    // own tile cell: keep the -z face velocity for the Lagrangian stage
-                    wz_prev = P::normal_velocity(fm[2], 2);
-                    if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
+                    for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
+                    if (i == tid) {
+                        // own tile cell: keep f' and the -z face velocity for S3
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) fown[f] = f1[f];
+                        wz_prev = P::normal_velocity(fm[2], 2);
+                        if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
+                    }
                 }
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
+                phim[c1] = re[(NR - 1) * R2 + c2];
             }
-#pragma unroll
-            for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
-            phim[c1] = re[(NR - 1) * R2 + c2];
         }
         __syncthreads();
+        // plane e is no longer read: its slot receives plane p + 1 during S3
+        if (p + 1 <= z1 + 1) issue_plane(p + 1);
         if (!active) continue;
         // ---- S3: Lagrangian fluxes of the own tile cell --------------------
         {
-            constexpr int NYF = Gm::YFH * W1;
             const int cx = own_tx + 1, cy = own_ty + 1;
             // face normal velocities W (gas: V stored first on every axis;
             // moments: u*_d is value d of an axis-d face)
@@ -493,14 +521,15 @@ fluid_step_kernel(StencilArgs<T> a) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T* F = fpb + f * R1;
-                const T fc = F[own_c1];
-                const T Fxm = Wxm * (Wxm > T(0) ? F[own_c1 - 1] : fc);
-                const T Fxp = Wxp * (Wxp > T(0) ? fc : F[own_c1 + 1]);
-                const T Fym = Wym * (Wym > T(0) ? F[own_c1 - W1] : fc);
-                const T Fyp = Wyp * (Wyp > T(0) ? fc : F[own_c1 + W1]);
+                const T fc = fown[f];
+                T uxm = fc, uxp = fc, uym = fc, uyp = fc;
+                if (Wxm > T(0)) uxm = F[own_c1 - 1];
+                if (!(Wxp > T(0))) uxp = F[own_c1 + 1];
+                if (Wym > T(0)) uym = F[own_c1 - W1];
+                if (!(Wyp > T(0))) uyp = F[own_c1 + W1];
                 const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
                 out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
-                acc[f] = fc - rat * ((Fxp - Fxm) + (Fyp - Fym)) + rat * Fzm;
+                acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
                 fprev[f] = fc;
             }
             const int l = e - 1;
@@ -512,6 +541,7 @@ fluid_step_kernel(StencilArgs<T> a) {
             }
         }
     }
+    cp_async_wait_all();
 
     // ---- block reduction of the conserved sums, kappa and the signal speed ----
     const int lane = tid & 31, warp = tid >> 5;

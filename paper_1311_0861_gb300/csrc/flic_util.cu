@@ -123,30 +123,63 @@ cudaError_t step_prep(double* scal, unsigned int* status, double dt, double cour
     return cudaGetLastError();
 }
 
-// One warp per quantity: lanes take blocks in a fixed stride (Neumaier sums),
-// then a fixed-order butterfly; the result does not depend on scheduling.
-__global__ void step_finalize_kernel(const double* __restrict__ pa, int na, const double* __restrict__ pb,
-                                     int nb, double h3, double* scal, unsigned int* status, flic_diag* d,
-                                     int count_step) {
-    __shared__ double res[Q_COUNT];
+// Deterministic two-level sum of the per-block partials.  Level 1: FIN_BLOCKS
+// blocks each sum a fixed contiguous range of rows (Neumaier compensation) and
+// reduce in a fixed order -- float64 throughput per SM is low on this part, so
+// the float64 work is spread over many SMs.  Level 2: one block sums the
+// FIN_BLOCKS rows in a fixed order and writes the record.
+constexpr int FIN_BLOCKS = FINALIZE_ROWS;
+
+template <int NTH>
+__device__ __forceinline__ void block_sum_rows(const double* __restrict__ pa, int na, const double* __restrict__ pb,
+                                               int nb, int r0, int r1, double* out /* [Q_COUNT] smem */) {
+    __shared__ double part[NTH / 32][Q_COUNT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < Q_COUNT; k += blockDim.x >> 5) {
-        double s = 0.0, c = 0.0;
-        for (int src = 0; src < 2; ++src) {
-            const double* p = src ? pb : pa;
-            const int n = src ? nb : na;
-            if (!p) continue;
-            for (int b = lane; b < n; b += 32) {
-                const double x = p[size_t(b) * Q_COUNT + k];
-                const double t = s + x;
-                c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-                s = t;
-            }
+    double s[Q_COUNT], c[Q_COUNT];
+#pragma unroll
+    for (int k = 0; k < Q_COUNT; ++k) { s[k] = 0.0; c[k] = 0.0; }
+    for (int r = r0 + threadIdx.x; r < r1; r += NTH) {
+        const double* p = (r < na) ? pa + size_t(r) * Q_COUNT : pb + size_t(r - na) * Q_COUNT;
+#pragma unroll
+        for (int k = 0; k < Q_COUNT; ++k) {
+            const double x = p[k];
+            const double t = s[k] + x;
+            c[k] += (fabs(s[k]) >= fabs(x)) ? (s[k] - t) + x : (x - t) + s[k];
+            s[k] = t;
         }
-        double v = s + c;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) res[k] = v * h3;
     }
+#pragma unroll
+    for (int k = 0; k < Q_COUNT; ++k) {
+        const double v = warp_sum(s[k] + c[k]);
+        if (lane == 0) part[warp][k] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < Q_COUNT; ++k) {
+            const double v = warp_sum(lane < NTH / 32 ? part[lane][k] : 0.0);
+            if (lane == 0) out[k] = v;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) finalize_level1(const double* __restrict__ pa, int na,
+                                                      const double* __restrict__ pb, int nb, double* level1) {
+    __shared__ double res[Q_COUNT];
+    const int rows = na + nb;
+    const int per = (rows + gridDim.x - 1) / gridDim.x;
+    const int r0 = min(rows, int(blockIdx.x) * per), r1 = min(rows, r0 + per);
+    block_sum_rows<256>(pa, na, pb, nb, r0, r1, res);
+    if (threadIdx.x < Q_COUNT) level1[size_t(blockIdx.x) * Q_COUNT + threadIdx.x] = res[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(64) step_finalize_kernel(const double* __restrict__ level1, double h3,
+                                                          double* scal, unsigned int* status, flic_diag* d,
+                                                          int count_step) {
+    __shared__ double res[Q_COUNT];
+    block_sum_rows<64>(level1, FIN_BLOCKS, nullptr, 0, 0, FIN_BLOCKS, res);
+    if (threadIdx.x < Q_COUNT) res[threadIdx.x] *= h3;
     __syncthreads();
     if (threadIdx.x == 0) {
         d->mass_gas = res[Q_MASS_GAS];
@@ -178,8 +211,9 @@ __global__ void step_finalize_kernel(const double* __restrict__ pa, int na, cons
 }
 
 cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
-                          unsigned int* status, flic_diag* diag, int count_step, cudaStream_t st) {
-    step_finalize_kernel<<<1, 128, 0, st>>>(pa, na, pb, nb, h3, scal, status, diag, count_step);
+                          unsigned int* status, flic_diag* diag, int count_step, double* level1, cudaStream_t st) {
+    finalize_level1<<<FIN_BLOCKS, 256, 0, st>>>(pa, na, pb, pb ? nb : 0, level1);
+    step_finalize_kernel<<<1, 64, 0, st>>>(level1, h3, scal, status, diag, count_step);
     return cudaGetLastError();
 }
 
