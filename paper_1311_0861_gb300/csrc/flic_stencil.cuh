@@ -15,9 +15,8 @@
 // Structure (2.5D z-march).  A block owns a TX x TY column tile and a chunk of
 // z planes.  It walks up the chunk with a two-plane ring of the input state in
 // shared memory over the tile plus a 2-cell halo (R2).  Per plane e:
-//   S0  asynchronous copy of plane e+1 into the ring (conserved fields + Phi;
-//       1/rho is filled in when the copy has landed), issued as soon as the
-//       slot's previous plane has been consumed so that it overlaps S3;
+//   S0  asynchronous 8-byte copies of plane e+2 into a three-slot ring (the
+//       fields the faces need, + Phi), one full iteration ahead of its use;
 //   S1  x- and y-face solutions of plane e over the tile plus a 1-cell halo (R1);
 //   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
 //   S3  upwind fluxes of f' for the tile cells; plane e-1 completes (its +z flux
@@ -70,24 +69,27 @@ template <> struct Acc<float> {
 // ---------------------------------------------------------------------------
 // physics policies
 // ---------------------------------------------------------------------------
-// Ring layout: ring[slot][field][R2 cell].  Face layout: face[value][...].
+// Ring layout: ring[slot][ring field][R2 cell]; the last ring field is Phi.
+// Face layout: face[value][...].  Reciprocal densities are formed at use.
 
 template <typename T>
 struct GasPhys {
     static constexpr int NF = 6;      // rho, mx, my, mz, E, e
-    static constexpr int NR = 8;      // ring: conserved 6 + 1/rho + Phi
+    static constexpr int NR = 7;      // ring: the 6 conserved fields + Phi
+    static constexpr int NEX = 0;     // fields read directly (not staged) by the Eulerian update
     static constexpr int NFACE = 2;   // V, P
-    static constexpr int R_IRHO = 6, R_PHI = 7;
+    static constexpr int R_PHI = 6;
     static constexpr int NQ = 8;      // accumulated quantities
-    static constexpr bool kR1Only(int) { return false; }
+    static __device__ __forceinline__ int ring_field(int r) { return r; }
+    static __device__ __forceinline__ int extra_field(int) { return 0; }
 
     // Eulerian face solution (Sec. 2.1) between ring cells a (left) and b (right)
     // along axis d.
     static __device__ __forceinline__ void face(const T* ra, int a, const T* rb, int b, int R2,
                                                 int d, T gamma, T* outv) {
         T rL = ra[0 * R2 + a], rR = rb[0 * R2 + b];
-        T vL = ra[(1 + d) * R2 + a] * ra[R_IRHO * R2 + a];
-        T vR = rb[(1 + d) * R2 + b] * rb[R_IRHO * R2 + b];
+        T vL = ra[(1 + d) * R2 + a] * rcp(rL);
+        T vR = rb[(1 + d) * R2 + b] * rcp(rR);
         T pL = (gamma - T(1)) * ra[5 * R2 + a];
         T pR = (gamma - T(1)) * rb[5 * R2 + b];
         T z2 = rL * rR * gamma * (pL + pR) * rcp(rL + rR);   // squared acoustic impedance
@@ -97,11 +99,11 @@ struct GasPhys {
         outv[1] = T(0.5) * (pL + pR) + T(0.5) * (vL - vR) * Z;    // P
     }
 
-    // Eulerian update of one cell.  fm[d], fp[d]: face values on the -d and +d
+    // Eulerian update of one cell.  fm[d], fpv[d]: face values on the -d and +d
     // faces; g[d]: central-difference gradient of Phi.
     static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
                                                  const T fpv[3][NFACE], const T g[3], T tau,
-                                                 T rat, T gamma, T* f1) {
+                                                 T rat, T gamma, const T*, T* f1) {
         T rho = r[0 * R2 + c];
         T m[3] = {r[1 * R2 + c], r[2 * R2 + c], r[3 * R2 + c]};
         T E = r[4 * R2 + c], e = r[5 * R2 + c];
@@ -123,13 +125,13 @@ struct GasPhys {
 
     // Conserved sums of the time-n state (tile cells).
     static __device__ __forceinline__ void accumulate_input(const T* r, int c, int R2, Acc<T>* q) {
-        T rho = r[0 * R2 + c], ir = r[R_IRHO * R2 + c];
+        T rho = r[0 * R2 + c];
         T mx = r[1 * R2 + c], my = r[2 * R2 + c], mz = r[3 * R2 + c];
         q[0].add(rho);
         q[1].add(mx);
         q[2].add(my);
         q[3].add(mz);
-        q[4].add(T(0.5) * (mx * mx + my * my + mz * mz) * ir);
+        q[4].add(T(0.5) * (mx * mx + my * my + mz * mz) * rcp(rho));
         q[5].add(r[5 * R2 + c]);
         q[6].add(T(0.5) * rho * r[R_PHI * R2 + c]);
     }
@@ -147,9 +149,11 @@ struct GasPhys {
         T cs = sqr_root(gamma * (gamma - T(1)) * e * ir);
         T vm = fmax(fabs(f[1]), fmax(fabs(f[2]), fabs(f[3]))) * ir + cs;
         vmax = fmax(vmax, vm);
-        bool ok = (f[0] > T(0)) && (e > T(0));
+        // every output is finite iff their sum is (no overflow at these magnitudes)
+        T sum = T(0);
 #pragma unroll
-        for (int i = 0; i < NF; ++i) ok = ok && finite_val(f[i]);
+        for (int i = 0; i < NF; ++i) sum += f[i];
+        bool ok = (f[0] > T(0)) && (e > T(0)) && finite_val(sum);
         bad = bad || !ok;
     }
 
@@ -164,12 +168,15 @@ template <typename T>
 struct BmePhys {
     // transported fields: n, qx, qy, qz, nExx, nEyy, nEzz, nExy, nExz, nEyz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz
     static constexpr int NF = 16;
-    static constexpr int NR = 18;     // ring: the 16 + 1/n + Phi
+    // ring: n, qx, qy, qz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz, Phi (what the faces need);
+    // the energy tensor nE is read directly by the Eulerian update
+    static constexpr int NR = 11;
+    static constexpr int NEX = 6;
     static constexpr int NFACE = 6;   // u*_x, u*_y, u*_z, Pi*_xd, Pi*_yd, Pi*_zd
-    static constexpr int R_IN = 16, R_PHI = 17;
+    static constexpr int R_P = 4, R_PHI = 10;
     static constexpr int NQ = 8;
-    // energy-tensor fields are only needed on R1 (Eulerian update), not for faces
-    static constexpr bool kR1Only(int f) { return f >= 4 && f < 10; }
+    static __device__ __forceinline__ int ring_field(int r) { return r < 4 ? r : r + 6; }
+    static __device__ __forceinline__ int extra_field(int k) { return 4 + k; }
 
     // index of tensor component (i, j) among (xx, yy, zz, xy, xz, yz)
     static __device__ __forceinline__ int tc(int i, int j) {
@@ -181,12 +188,12 @@ struct BmePhys {
                                                 int d, T, T* outv) {
         const int t1 = (d == 0) ? 1 : 0;
         const int t2 = (d == 2) ? 1 : 2;
-        T inL = ra[R_IN * R2 + a], inR = rb[R_IN * R2 + b];
         T nL = ra[0 * R2 + a], nR = rb[0 * R2 + b];
+        T inL = rcp(nL), inR = rcp(nR);
         T unL = ra[(1 + d) * R2 + a] * inL, unR = rb[(1 + d) * R2 + b] * inR;
         T u1L = ra[(1 + t1) * R2 + a] * inL, u1R = rb[(1 + t1) * R2 + b] * inR;
         T u2L = ra[(1 + t2) * R2 + a] * inL, u2R = rb[(1 + t2) * R2 + b] * inR;
-        const int pnn = 10 + tc(d, d), pn1 = 10 + tc(d, t1), pn2 = 10 + tc(d, t2);
+        const int pnn = R_P + tc(d, d), pn1 = R_P + tc(d, t1), pn2 = R_P + tc(d, t2);
         T PnnL = ra[pnn * R2 + a], PnnR = rb[pnn * R2 + b];
         T P1L = ra[pn1 * R2 + a], P1R = rb[pn1 * R2 + b];
         T P2L = ra[pn2 * R2 + a], P2R = rb[pn2 * R2 + b];
@@ -204,28 +211,23 @@ struct BmePhys {
         T dun = T(0.5) * (unL - unR);
         T cu = dPnn * (T(1) - s3) * iA * iz1;   // multiplies b_k in u_t
         T cp = dun * rho * (s3 - T(1)) * iz2;   // multiplies b_k in Pi_nt
-        T un = T(0.5) * (unL + unR) + dPnn * iz1;
-        T u1 = T(0.5) * (u1L + u1R) + T(0.5) * (P1L - P1R) * iz2 + b1 * cu;
-        T u2 = T(0.5) * (u2L + u2R) + T(0.5) * (P2L - P2R) * iz2 + b2 * cu;
-        T Pnn = A + dun * Z1;
-        T P1 = b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp;
-        T P2 = b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp;
-        outv[d] = un;
-        outv[t1] = u1;
-        outv[t2] = u2;
-        outv[3 + d] = Pnn;
-        outv[3 + t1] = P1;
-        outv[3 + t2] = P2;
+        outv[d] = T(0.5) * (unL + unR) + dPnn * iz1;
+        outv[t1] = T(0.5) * (u1L + u1R) + T(0.5) * (P1L - P1R) * iz2 + b1 * cu;
+        outv[t2] = T(0.5) * (u2L + u2R) + T(0.5) * (P2L - P2R) * iz2 + b2 * cu;
+        outv[3 + d] = A + dun * Z1;
+        outv[3 + t1] = b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp;
+        outv[3 + t2] = b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp;
     }
 
+    // nE: the cell's energy tensor (6 components, read directly from global memory)
     static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
                                                  const T fpv[3][NFACE], const T g[3], T tau,
-                                                 T rat, T, T* f1) {
+                                                 T rat, T, const T* nE, T* f1) {
         T n = r[0 * R2 + c];
         T q[3] = {r[1 * R2 + c], r[2 * R2 + c], r[3 * R2 + c]};
         T Pi[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) Pi[k] = r[(10 + k) * R2 + c];
+        for (int k = 0; k < 6; ++k) Pi[k] = r[(R_P + k) * R2 + c];
         f1[0] = n;
         // momentum: q_i -= r sum_d delta_d Pi*_{id} + tau n dPhi/dx_i
 #pragma unroll
@@ -252,8 +254,7 @@ struct BmePhys {
                     - (fm[d][3 + j] * fm[d][i] + fm[d][3 + i] * fm[d][j]);
                 sP += Pi[tc(j, d)] * du[d][i] + Pi[tc(i, d)] * du[d][j];
             }
-            T nE = r[(4 + k) * R2 + c];
-            f1[4 + k] = nE - rat * sE - tau * (q[i] * g[j] + q[j] * g[i]);
+            f1[4 + k] = nE[k] - rat * sE - tau * (q[i] * g[j] + q[j] * g[i]);
             f1[10 + k] = Pi[k] - rat * sP;
         }
     }
@@ -261,14 +262,14 @@ struct BmePhys {
     static __device__ __forceinline__ T normal_velocity(const T* facev, int d) { return facev[d]; }
 
     static __device__ __forceinline__ void accumulate_input(const T* r, int c, int R2, Acc<T>* q) {
-        T n = r[0 * R2 + c], in = r[R_IN * R2 + c];
+        T n = r[0 * R2 + c];
         T qx = r[1 * R2 + c], qy = r[2 * R2 + c], qz = r[3 * R2 + c];
         q[0].add(n);
         q[1].add(qx);
         q[2].add(qy);
         q[3].add(qz);
-        q[4].add(T(0.5) * (qx * qx + qy * qy + qz * qz) * in);
-        q[5].add(T(0.5) * (r[10 * R2 + c] + r[11 * R2 + c] + r[12 * R2 + c]));
+        q[4].add(T(0.5) * (qx * qx + qy * qy + qz * qz) * rcp(n));
+        q[5].add(T(0.5) * (r[(R_P + 0) * R2 + c] + r[(R_P + 1) * R2 + c] + r[(R_P + 2) * R2 + c]));
         q[6].add(T(0.5) * n * r[R_PHI * R2 + c]);
     }
 
@@ -297,9 +298,10 @@ struct BmePhys {
         for (int d = 0; d < 3; ++d)
             vm = fmax(vm, fabs(f[1 + d]) * in + sqr_root(T(3) * f[10 + d] * in));
         vmax = fmax(vmax, vm);
-        bool ok = (f[0] > T(0)) && (f[10] > T(0)) && (f[11] > T(0)) && (f[12] > T(0));
+        T sum = T(0);
 #pragma unroll
-        for (int i = 0; i < NF; ++i) ok = ok && finite_val(f[i]);
+        for (int i = 0; i < NF; ++i) sum += f[i];
+        bool ok = (f[0] > T(0)) && (f[10] > T(0)) && (f[11] > T(0)) && (f[12] > T(0)) && finite_val(sum);
         bad = bad || !ok;
     }
 
@@ -312,25 +314,35 @@ struct BmePhys {
 // ---------------------------------------------------------------------------
 // shared-memory geometry of a tile
 // ---------------------------------------------------------------------------
-template <class P, typename T, int TX, int TY>
+constexpr int RING_SLOTS = 3;   // planes e, e+1 in use, e+2 in flight
+
+template <class P, typename T, int TX, int TY, bool SEX>
 struct Geom {
     static constexpr int NT = TX * TY;
     static constexpr int W2 = TX + 4, H2 = TY + 4, R2 = W2 * H2;   // tile + 2 halo
     static constexpr int W1 = TX + 2, H1 = TY + 2, R1 = W1 * H1;   // tile + 1 halo
     static constexpr int XFW = TX + 3;                               // x faces per R1 row
     static constexpr int YFH = TY + 3;                               // y-face rows
-    static constexpr size_t ring_elems = size_t(2) * P::NR * R2;
+    static constexpr int CH = 8 / sizeof(T);                         // elements per 8-byte copy
+    static constexpr int CPR = W2 / CH;                              // copies per ring row
+    static_assert(W2 % CH == 0, "ring rows must split into 8-byte copies");
+    static constexpr size_t ring_elems = size_t(RING_SLOTS) * P::NR * R2;
     static constexpr size_t xf_elems = size_t(P::NFACE) * H1 * XFW;
     static constexpr size_t yf_elems = size_t(P::NFACE) * YFH * W1;
     static constexpr size_t zc_elems = size_t(P::NFACE) * R1;
     static constexpr size_t fp_elems = size_t(P::NF) * R1;
     static constexpr size_t phim_elems = R1;
+    // fields read only by the Eulerian update (moment energy tensor), staged
+    // over the R1 rows in two slots when SEX
+    static constexpr size_t ex_slot = size_t(P::NEX) * H1 * W2;
+    static constexpr size_t ex_elems = SEX ? 2 * ex_slot : 0;
     // the double-precision reduction scratch starts on a 16-byte boundary,
-    // followed by the wrapped-coordinate tables (W2 + H2 ints)
+    // followed by the wrapped-coordinate tables (CPR + H2 ints)
     static constexpr size_t red_offset =
-        ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems) * sizeof(T) + 15) / 16 * 16;
+        ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems + ex_elems) * sizeof(T) + 15) /
+        16 * 16;
     static constexpr size_t tab_offset = red_offset + sizeof(double) * 32 * (P::NQ + 1);
-    static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (W2 + H2);
+    static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (CPR + H2);
 };
 
 // R1 cell i -> (jx, jy), tile cells first (so that i == threadIdx.x is the
@@ -353,25 +365,27 @@ __device__ __forceinline__ void r1_coords(int i, int& jx, int& jy) {
     jy = 1 + h;
 }
 
-// Asynchronous 4- or 8-byte global -> shared copy (no register staging).
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+// Asynchronous 8-byte global -> shared copy (no register staging) and group
+// bookkeeping.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <class P, typename T, int TX, int TY, int MINB>
+__device__ __forceinline__ int ring_slot(int p) { return ((p % RING_SLOTS) + RING_SLOTS) % RING_SLOTS; }
+
+template <class P, typename T, int TX, int TY, int MINB, bool SEX>
 __global__ void __launch_bounds__(TX * TY, MINB)
 fluid_step_kernel(StencilArgs<T> a) {
-    using Gm = Geom<P, T, TX, TY>;
+    using Gm = Geom<P, T, TX, TY, SEX>;
     constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, H2 = Gm::H2, R1 = Gm::R1, W1 = Gm::W1;
-    constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE;
+    constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE, NEX = P::NEX;
     constexpr int NXF = Gm::H1 * Gm::XFW;
     constexpr int NYF = Gm::YFH * W1;
+    constexpr int CH = Gm::CH, CPR = Gm::CPR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);
     T* xf = ring + Gm::ring_elems;
@@ -379,9 +393,10 @@ fluid_step_kernel(StencilArgs<T> a) {
     T* zc = yf + Gm::yf_elems;
     T* fpb = zc + Gm::zc_elems;
     T* phim = fpb + Gm::fp_elems;
+    T* exb = phim + Gm::phim_elems;
     double* red = reinterpret_cast<double*>(smem_raw + Gm::red_offset);
-    int* xoff = reinterpret_cast<int*>(smem_raw + Gm::tab_offset);   // wrapped x of R2 columns
-    int* yoff = xoff + W2;                                             // wrapped y * N of R2 rows
+    int* xoff = reinterpret_cast<int*>(smem_raw + Gm::tab_offset);   // wrapped x of each 8-byte column chunk
+    int* yoff = xoff + CPR;                                            // wrapped y * N of R2 rows
 
     const int tid = threadIdx.x;
     const int N = a.n;
@@ -396,7 +411,8 @@ fluid_step_kernel(StencilArgs<T> a) {
     const T half_ih = T(0.5 * a.inv_h);
     const T gamma = a.gamma, eta = a.eta;
 
-    for (int i = tid; i < W2; i += NT) xoff[i] = wrap_mod(x0 + i - 2, N);
+    // x0 - 2 and N are multiples of CH, so no chunk straddles the periodic wrap
+    for (int i = tid; i < CPR; i += NT) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
     for (int i = tid; i < H2; i += NT) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
     __syncthreads();
 
@@ -404,29 +420,49 @@ fluid_step_kernel(StencilArgs<T> a) {
     const int own_tx = tid % TX, own_ty = tid / TX;
     const bool own_valid = (x0 + own_tx < N) && (y0 + own_ty < N);
     const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
-    const size_t own_g = size_t(yoff[own_ty + 2]) + xoff[own_tx + 2];
 
-    // S0 of plane pz: asynchronous copies into ring slot pz & 1 (conserved
-    // fields and Phi; 1/rho is filled in after the copies land).
+    // S0 of plane pz: asynchronous 8-byte copies of the ring fields of the plane
+    // (tile + 2-cell halo) into its ring slot, committed as one group.  Each
+    // thread owns fixed (row, chunk) positions and walks the fields.
+    constexpr int NPOS = H2 * CPR;
     auto issue_plane = [&](int pz) {
-        T* dst = ring + (pz & 1) * NR * R2;
-        const size_t zoff = size_t(wrap_mod(pz, N)) * plane;
-        for (int i = tid; i < R2; i += NT) {
-            const int ix = i % W2, iy = i / W2;
-            const bool r1 = (ix >= 1) && (ix <= TX + 2) && (iy >= 1) && (iy <= TY + 2);
-            const size_t g = zoff + size_t(yoff[iy]) + xoff[ix];
+        T* dst = ring + ring_slot(pz) * NR * R2;
+        const int zw = pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
+        const size_t zoff = size_t(zw) * plane;
+        for (int pos = tid; pos < NPOS; pos += NT) {
+            const int iy = pos / CPR, c = pos % CPR;
+            T* d = dst + iy * W2 + c * CH;
+            const size_t goff = zoff + size_t(yoff[iy]) + xoff[c];
+            const T* src = a.in + goff;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                if (P::kR1Only(f) && !r1) continue;
-                cp_async_elem(dst + f * R2 + i, a.in + f * a.fs + g);
-            }
-            cp_async_elem(dst + (NR - 1) * R2 + i, a.phi + g);
+            for (int r = 0; r < NR - 1; ++r) cp_async8(d + r * R2, src + size_t(P::ring_field(r)) * a.fs);
+            cp_async8(d + (NR - 1) * R2, a.phi + goff);
+        }
+        cp_async_commit();
+    };
+    // extra fields of plane pz over the R1 rows into slot pz & 1 (same group as
+    // the ring copy issued in the same iteration)
+    constexpr int NPOS1 = Gm::H1 * CPR;
+    auto issue_extra = [&](int pz) {
+        T* dst = exb + (pz & 1) * Gm::ex_slot;
+        const int zw = pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
+        const size_t zoff = size_t(zw) * plane;
+        for (int pos = tid; pos < NPOS1; pos += NT) {
+            const int jy = pos / CPR, c = pos % CPR;
+            T* d = dst + jy * W2 + c * CH;
+            const T* src = a.in + zoff + size_t(yoff[jy + 1]) + xoff[c];
+#pragma unroll
+            for (int k = 0; k < NEX; ++k)
+                cp_async8(d + k * Gm::H1 * W2, src + size_t(P::extra_field(k)) * a.fs);
         }
     };
+    // global x of R2 column ix (chunks never straddle the wrap)
+    auto gx = [&](int ix) { return xoff[ix / CH] + ix % CH; };
 
-    T fprev[NF], acc[NF], fown[NF];
+    const size_t own_g = size_t(yoff[own_ty + 2]) + gx(own_tx + 2);
+    T fprev[NF], acc[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); fown[f] = T(0); }
+    for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); }
     T wz_prev = T(0);
     Acc<T> q[P::NQ];
     T vmax = T(0);
@@ -434,14 +470,22 @@ fluid_step_kernel(StencilArgs<T> a) {
 
     issue_plane(z0 - 2);
     for (int p = z0 - 2; p <= z1 + 1; ++p) {
-        T* rp = ring + (p & 1) * NR * R2;        // plane p
-        T* re = ring + ((p - 1) & 1) * NR * R2;  // plane e = p - 1
+        const T* rp = ring + ring_slot(p) * NR * R2;       // plane p
+        const T* re = ring + ring_slot(p - 1) * NR * R2;   // plane e = p - 1
         const int e = p - 1;
         const bool active = (p >= z0);
-        cp_async_wait_all();
+        // plane p + 1 goes into the slot of plane p - 2 (last read by S2 of the
+        // previous iteration, before its closing barrier)
+        if (p + 1 <= z1 + 1) {
+            // the extra fields of plane p are read by S2 of the next iteration
+            if (SEX && NEX > 0 && p >= z0 - 1) issue_extra(p);
+            issue_plane(p + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
-        // ---- 1/rho of plane p; S1: x/y faces of plane e ----------------------
-        for (int i = tid; i < R2; i += NT) rp[(NR - 2) * R2 + i] = rcp(rp[i]);
+        // ---- S1: x/y faces of plane e ---------------------------------------
         if (active) {
             for (int i = tid; i < NXF; i += NT) {
                 const int fx = i % Gm::XFW, jy = i / Gm::XFW;
@@ -463,11 +507,24 @@ fluid_step_kernel(StencilArgs<T> a) {
         __syncthreads();
         // ---- S2: z face e+1/2 and Eulerian update of plane e over R1 ---------
         if (p >= z0 - 1) {
+            const size_t zoff_e = size_t(e < 0 ? e + N : (e >= N ? e - N : e)) * plane;
             for (int i = tid; i < R1; i += NT) {
                 int jx, jy;
                 r1_coords<TX, TY>(i, jx, jy);
                 const int c1 = jy * W1 + jx;
                 const int c2 = (jy + 1) * W2 + jx + 1;
+                T ex[NEX > 0 ? NEX : 1];
+                if (active) {
+                    if (SEX) {
+                        const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
+#pragma unroll
+                        for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
+                    } else {
+                        const size_t g = zoff_e + size_t(yoff[jy + 1]) + gx(jx + 1);
+#pragma unroll
+                        for (int k = 0; k < NEX; ++k) ex[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
+                    }
+                }
                 T zn[NFACE];
                 P::face(re, c2, rp, c2, R2, 2, gamma, zn);
                 if (active) {
@@ -482,29 +539,25 @@ fluid_step_kernel(StencilArgs<T> a) {
                         fpv[2][k] = zn[k];
                     }
                     T g[3];
-                    g[0] = (re[(NR - 1) * R2 + c2 + 1] - re[(NR - 1) * R2 + c2 - 1]) * half_ih;
-                    g[1] = (re[(NR - 1) * R2 + c2 + W2] - re[(NR - 1) * R2 + c2 - W2]) * half_ih;
-                    g[2] = (rp[(NR - 1) * R2 + c2] - phim[c1]) * half_ih;
+                    g[0] = (re[P::R_PHI * R2 + c2 + 1] - re[P::R_PHI * R2 + c2 - 1]) * half_ih;
+                    g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
+                    g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
                     T f1[NF];
-                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, f1);
+                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
 #pragma unroll
                     for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
                     if (i == tid) {
-                        // own tile cell: keep f' and the -z face velocity for S3
-#pragma unroll
-                        for (int f = 0; f < NF; ++f) fown[f] = f1[f];
+                        // own tile cell: keep the -z face velocity for S3
                         wz_prev = P::normal_velocity(fm[2], 2);
                         if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
                     }
                 }
 #pragma unroll
                 for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
-                phim[c1] = re[(NR - 1) * R2 + c2];
+                phim[c1] = re[P::R_PHI * R2 + c2];
             }
         }
         __syncthreads();
-        // plane e is no longer read: its slot receives plane p + 1 during S3
-        if (p + 1 <= z1 + 1) issue_plane(p + 1);
         if (!active) continue;
         // ---- S3: Lagrangian fluxes of the own tile cell --------------------
         {
@@ -521,7 +574,7 @@ fluid_step_kernel(StencilArgs<T> a) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T* F = fpb + f * R1;
-                const T fc = fown[f];
+                const T fc = F[own_c1];
                 T uxm = fc, uxp = fc, uym = fc, uyp = fc;
                 if (Wxm > T(0)) uxm = F[own_c1 - 1];
                 if (!(Wxp > T(0))) uxp = F[own_c1 + 1];
@@ -541,7 +594,7 @@ fluid_step_kernel(StencilArgs<T> a) {
             }
         }
     }
-    cp_async_wait_all();
+    cp_async_wait<0>();
 
     // ---- block reduction of the conserved sums, kappa and the signal speed ----
     const int lane = tid & 31, warp = tid >> 5;
