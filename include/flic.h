@@ -150,6 +150,32 @@ int flic_step_diagnostics(flic_handle* h, flic_diag* out);
  * current state; dt = 0). */
 int flic_diagnostics(flic_handle* h, flic_diag* out);
 
+/* Diagnostics of a caller-owned float64 state with NO device allocation (no
+ * counterpart in the paper: this is a deployment entry point).
+ *
+ * For callers that cannot call cudaMalloc -- code running while another owner
+ * has reserved the device memory (an in-situ analysis hook inside a simulation
+ * that pre-allocates the GPU), or a latency-critical path that cannot take an
+ * allocation's implicit device synchronisation.  It computes what
+ * flic_diagnostics computes (conserved sums, kappa_gas, kappa_bme, signal speed,
+ * validity) for 22 device float64 arrays of n^3 cells (field order and layout
+ * above) and, when phi (device, n^3 float64) is not NULL, E_pot; dt = 0,
+ * step = 0, time = 0.  The result is written to the host record *out.
+ *
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * about 102 KiB (1024 partial rows) that every GPU loading the library keeps
+ * until exit; n must be between 1 and 1024, larger grids are rejected with
+ * FLIC_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  Every call shares the array and leaves the last call's
+ * contents in it; the scalars that must start at zero are cleared on entry.
+ * Calls that overlap on the GPU (different streams or threads) race on it.
+ * Runs on `stream` (cudaStream_t, NULL = legacy default stream) and waits for
+ * it.  Errors: INVALID_ARG, CUDA (message in flic_last_error(NULL)),
+ * NONPHYSICAL (record still written). */
+int flic_state_diagnostics_noalloc(const double* const fields[FLIC_NFIELDS], const double* phi, int n, double h,
+                                   double gamma, void* stream, flic_diag* out);
+
 /* Waits for all work of the handle. */
 int flic_sync(flic_handle* h);
 

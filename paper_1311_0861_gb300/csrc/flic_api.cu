@@ -45,6 +45,10 @@ struct flic_handle {
 
 static std::string g_init_err;
 
+namespace flic {
+void set_global_error(const char* msg) { g_init_err = msg; }
+}  // namespace flic
+
 #define FLIC_CK(h, call)                                                                     \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \

@@ -29,10 +29,23 @@ template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const Step
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);
 template <typename T> cudaError_t convert_out(const T* src, double* dst, size_t n, cudaStream_t st);
 
-// Conserved sums, kappa and signal speed of a whole state (partials[nb][Q_COUNT]).
+// The 22 field arrays of a state.
+template <typename T>
+struct FieldPtrs {
+    const T* f[F_COUNT];
+};
+
+// Conserved sums, kappa and signal speed of a whole state (partials[nb][Q_COUNT];
+// phi may be null, E_pot then sums to zero).
 template <typename T>
 cudaError_t state_reduce(const T* state, size_t fs, const T* phi, size_t cells, double gamma,
                          double* partials, int nb, double* vmax, unsigned int* status, cudaStream_t st);
+template <typename T>
+cudaError_t state_reduce(const FieldPtrs<T>& fields, const T* phi, size_t cells, double gamma, double* partials,
+                         int nb, double* vmax, unsigned int* status, cudaStream_t st);
+
+// Message returned by flic_last_error(NULL).
+void set_global_error(const char* msg);
 
 // Device scalars of a handle.
 enum Scalar { S_VMAX_CUR = 0, S_TAU, S_VMAX_NEXT, S_TIME, S_COUNT = 8 };

@@ -30,9 +30,8 @@ template cudaError_t convert_out<double>(const double*, double*, size_t, cudaStr
 // Conserved sums, kappa (Sec. 2.4) and signal speed of a whole state; one row of
 // Q_COUNT partial sums per block, plus an atomic max and the validity bit.
 template <typename T>
-__global__ void state_reduce_kernel(const T* __restrict__ s, size_t fs, const T* __restrict__ phi,
-                                    size_t cells, T gamma, double* partials, double* vmax,
-                                    unsigned int* status) {
+__global__ void state_reduce_kernel(FieldPtrs<T> s, const T* __restrict__ phi, size_t cells, T gamma,
+                                    double* partials, double* vmax, unsigned int* status) {
     __shared__ double red[32][Q_COUNT + 1];
     Acc<T> q[Q_COUNT];
     T vm = T(0);
@@ -41,7 +40,7 @@ __global__ void state_reduce_kernel(const T* __restrict__ s, size_t fs, const T*
          c += size_t(gridDim.x) * blockDim.x) {
         T f[F_COUNT];
 #pragma unroll
-        for (int k = 0; k < F_COUNT; ++k) f[k] = s[k * fs + c];
+        for (int k = 0; k < F_COUNT; ++k) f[k] = s.f[k][c];
         const T ir = rcp(f[F_RHO]), in = rcp(f[F_N]);
         const T K = T(0.5) * (f[F_MX] * f[F_MX] + f[F_MY] * f[F_MY] + f[F_MZ] * f[F_MZ]) * ir;
         const T Kb = T(0.5) * (f[F_QX] * f[F_QX] + f[F_QY] * f[F_QY] + f[F_QZ] * f[F_QZ]) * in;
@@ -54,7 +53,7 @@ __global__ void state_reduce_kernel(const T* __restrict__ s, size_t fs, const T*
         q[Q_EINT_GAS].add(f[F_EINT]);
         q[Q_EKIN_BME].add(Kb);
         q[Q_ETHERM_BME].add(T(0.5) * (f[F_PXX] + f[F_PYY] + f[F_PZZ]));
-        q[Q_EPOT].add(T(0.5) * (f[F_RHO] + f[F_N]) * phi[c]);
+        if (phi) q[Q_EPOT].add(T(0.5) * (f[F_RHO] + f[F_N]) * phi[c]);
         q[Q_KAPPA_GAS].add(fabs(f[F_E] - f[F_EINT] - K));
         T kb = T(0);
 #pragma unroll
@@ -101,14 +100,24 @@ __global__ void state_reduce_kernel(const T* __restrict__ s, size_t fs, const T*
 }
 
 template <typename T>
+cudaError_t state_reduce(const FieldPtrs<T>& fields, const T* phi, size_t cells, double gamma, double* partials,
+                         int nb, double* vmax, unsigned int* status, cudaStream_t st) {
+    state_reduce_kernel<T><<<nb, 256, 0, st>>>(fields, phi, cells, T(gamma), partials, vmax, status);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t state_reduce(const T* state, size_t fs, const T* phi, size_t cells, double gamma,
                          double* partials, int nb, double* vmax, unsigned int* status, cudaStream_t st) {
-    state_reduce_kernel<T><<<nb, 256, 0, st>>>(state, fs, phi, cells, T(gamma), partials, vmax, status);
-    return cudaGetLastError();
+    FieldPtrs<T> f;
+    for (int k = 0; k < F_COUNT; ++k) f.f[k] = state + size_t(k) * fs;
+    return state_reduce<T>(f, phi, cells, gamma, partials, nb, vmax, status, st);
 }
 template cudaError_t state_reduce<float>(const float*, size_t, const float*, size_t, double, double*, int,
                                          double*, unsigned int*, cudaStream_t);
 template cudaError_t state_reduce<double>(const double*, size_t, const double*, size_t, double, double*, int,
+                                          double*, unsigned int*, cudaStream_t);
+template cudaError_t state_reduce<double>(const FieldPtrs<double>&, const double*, size_t, double, double*, int,
                                           double*, unsigned int*, cudaStream_t);
 
 __global__ void step_prep_kernel(double* scal, unsigned int* status, double dt, double courant_h) {

@@ -30,7 +30,8 @@ PERIODIC, ISOLATED = 0, 1
 EXPORTS = ("flic_init_grid", "flic_set_state", "flic_set_state_device", "flic_get_state",
            "flic_get_state_device", "flic_step", "flic_run", "flic_solve_poisson",
            "flic_step_diagnostics", "flic_diagnostics", "flic_sync", "flic_destroy",
-           "flic_last_error", "flic_version", "flic_profile", "flic_launches_per_step")
+           "flic_last_error", "flic_version", "flic_profile", "flic_launches_per_step",
+           "flic_state_diagnostics_noalloc")
 NSTAGES = 4
 STAGES = ("poisson", "gas", "bme", "finalize")
 
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.flic_profile.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double)]
     lib.flic_launches_per_step.argtypes = [P]
+    lib.flic_state_diagnostics_noalloc.argtypes = [ctypes.POINTER(P), P, ctypes.c_int, ctypes.c_double,
+                                                   ctypes.c_double, P, ctypes.POINTER(Diag)]
     lib.flic_step_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
     lib.flic_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
     lib.flic_sync.argtypes = [P]
@@ -120,6 +123,33 @@ def _field_list(state, n):
         if tuple(a.shape) != (n, n, n) and int(np.prod(a.shape)) != n ** 3:
             raise FlicError(ERR_INVALID_ARG, f"field shape {tuple(a.shape)} != ({n},{n},{n})")
     return arrs
+
+
+def state_diagnostics_noalloc(fields, phi, n: int, h: float, gamma: float = 5.0 / 3.0, stream: int = 0,
+                              allow_nonphysical: bool = False) -> dict:
+    """Diagnostics of 22 caller-owned device float64 arrays (and an optional
+    device potential) through flic_state_diagnostics_noalloc, which allocates no
+    device memory (for callers that cannot allocate; see include/flic.h)."""
+    lib = load()
+    arrs = _field_list(fields, n)
+    ptrs = []
+    for a in arrs:
+        p, dev = _ptr_of(a, True)
+        if not dev:
+            raise FlicError(ERR_INVALID_ARG, "fields must be device arrays")
+        ptrs.append(p)
+    pp = None
+    if phi is not None:
+        pp, dev = _ptr_of(phi, True)
+        if not dev:
+            raise FlicError(ERR_INVALID_ARG, "phi must be a device array")
+    d = Diag()
+    rc = lib.flic_state_diagnostics_noalloc((ctypes.c_void_p * NFIELDS)(*ptrs), ctypes.c_void_p(pp), int(n),
+                                            float(h), float(gamma), ctypes.c_void_p(stream or None),
+                                            ctypes.byref(d))
+    if rc != OK and not (rc == ERR_NONPHYSICAL and allow_nonphysical):
+        raise FlicError(rc, lib.flic_last_error(None).decode())
+    return d.as_dict()
 
 
 class Grid:
