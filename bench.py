@@ -283,12 +283,16 @@ def main(argv=None):
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3}
+    # ncu DRAM bytes per launch, recorded for a given kernel source: used only
+    # while the kernel source is unchanged
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_file):
         try:
-            t = json.load(open(traffic_file)).get(f"{kern}-{args.precision}-{N}")
-            if t:
-                roofline["traffic"] = t
+            import hashlib
+            rec = json.load(open(traffic_file))
+            src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == rec["sha256_16"]:
+                roofline["traffic"] = rec.get(f"{kern}-{args.precision}-{N}")
         except Exception:
             pass
 
