@@ -60,7 +60,9 @@ enum flic_precision {
 
 enum flic_poisson_bc {
     FLIC_PERIODIC = 0,   /* periodic potential, 27-point symbol (Sec. 2.3) */
-    FLIC_ISOLATED = 1    /* zero-padded (2N)^3 convolution with -G h^3/|r| (reserved) */
+    FLIC_ISOLATED = 1    /* vacuum boundaries: zero-padded (2N)^3 convolution with the point-mass
+                            Green's function -G h^3/|r|, -G h^2 (3 ln(2+sqrt 3) - pi/2) at r = 0
+                            (n = 8..128, 256, 512); the hydrodynamics stays periodic */
 };
 
 typedef struct flic_grid_desc {

@@ -26,6 +26,8 @@ struct flic_handle {
     void* tw = nullptr;
     int tw_len = 0;
     void* asin2 = nullptr;
+    void* gtab = nullptr;             // isolated mode: scaled transform of the Green's function, (N+1)^3
+    bool iso = false;
     FftPlans plans;
     double* scal = nullptr;
     unsigned int* status = nullptr;
@@ -75,9 +77,14 @@ template <typename T>
 static int enqueue_poisson(flic_handle* h) {
     if (h->d.G == 0.0) return FLIC_OK;   // phi stays zero
     const T* s = reinterpret_cast<const T*>(h->state[h->cur]);
-    FLIC_CK(h, poisson_periodic<T>(s + F_RHO * h->fs, s + F_N * h->fs, reinterpret_cast<T*>(h->phi), h->spec,
-                                   h->N, h->plans, h->tw, h->tw_len, reinterpret_cast<const T*>(h->asin2),
-                                   h->d.G * h->h * h->h, h->st));
+    if (h->iso) {
+        FLIC_CK(h, poisson_isolated<T>(s + F_RHO * h->fs, s + F_N * h->fs, reinterpret_cast<T*>(h->phi), h->spec,
+                                       h->N, h->tw, reinterpret_cast<const T*>(h->gtab), h->st));
+    } else {
+        FLIC_CK(h, poisson_periodic<T>(s + F_RHO * h->fs, s + F_N * h->fs, reinterpret_cast<T*>(h->phi), h->spec,
+                                       h->N, h->plans, h->tw, h->tw_len, reinterpret_cast<const T*>(h->asin2),
+                                       h->d.G * h->h * h->h, h->st));
+    }
     return FLIC_OK;
 }
 
@@ -189,7 +196,7 @@ static void free_all(flic_handle* h) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
         if (h->state[i]) cudaFree(h->state[i]);
     }
-    void* bufs[] = {h->phi, h->spec, h->tw, h->asin2, h->scal, h->status, h->part_gas, h->part_bme,
+    void* bufs[] = {h->phi, h->spec, h->tw, h->asin2, h->gtab, h->scal, h->status, h->part_gas, h->part_bme,
                     h->part_diag, h->level1, h->diag_dev, h->staging};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -205,8 +212,10 @@ static int init_impl(flic_handle* h) {
     h->fs = (h->cells + 63) / 64 * 64;
     h->esz = sizeof(T);
     if (fft_plan_init(N, &h->plans)) { h->err = "unsupported FFT length"; return FLIC_ERR_INVALID_ARG; }
+    if (h->iso && !fft_iso_supported(N)) { h->err = "unsupported size for the isolated solve"; return FLIC_ERR_INVALID_ARG; }
     FLIC_CK(h, stencil_prepare<T>());
     FLIC_CK(h, fft_prepare<T>(N));
+    if (h->iso) FLIC_CK(h, fft_prepare_iso<T>(N));
     h->gcfg = gas_cfg<T>(N, 0);
     h->bcfg = bme_cfg<T>(N, 0);
     h->nb_diag = 152 * 4;
@@ -216,17 +225,18 @@ static int init_impl(flic_handle* h) {
     }
     FLIC_CK(h, cudaMalloc(&h->phi, h->fs * sizeof(T)));
     FLIC_CK(h, cudaMemsetAsync(h->phi, 0, h->fs * sizeof(T), h->st));
-    FLIC_CK(h, cudaMalloc(&h->spec, size_t(N) * N * (N / 2 + 1) * sizeof(C)));
-    h->tw_len = N;
+    const int L = h->iso ? 2 * N : N;   // transform length
+    FLIC_CK(h, cudaMalloc(&h->spec, size_t(N) * L * (L / 2 + 1) * sizeof(C)));
+    h->tw_len = L;
     {
-        C* tw = new C[N];
-        for (int j = 0; j < N; ++j) {
-            const long double ang = 2.0L * 3.141592653589793238462643383279502884L * j / N;
+        C* tw = new C[L];
+        for (int j = 0; j < L; ++j) {
+            const long double ang = 2.0L * 3.141592653589793238462643383279502884L * j / L;
             tw[j].x = T(std::cos(ang));
             tw[j].y = T(-std::sin(ang));
         }
-        cudaError_t e = cudaMalloc(&h->tw, N * sizeof(C));
-        if (e == cudaSuccess) e = cudaMemcpy(h->tw, tw, N * sizeof(C), cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMalloc(&h->tw, L * sizeof(C));
+        if (e == cudaSuccess) e = cudaMemcpy(h->tw, tw, L * sizeof(C), cudaMemcpyHostToDevice);
         delete[] tw;
         FLIC_CK(h, e);
         T* a2 = new T[N];
@@ -237,6 +247,21 @@ static int init_impl(flic_handle* h) {
         e = cudaMalloc(&h->asin2, N * sizeof(T));
         if (e == cudaSuccess) e = cudaMemcpy(h->asin2, a2, N * sizeof(T), cudaMemcpyHostToDevice);
         delete[] a2;
+        FLIC_CK(h, e);
+    }
+    if (h->iso) {
+        // transform of the Green's function, computed once with temporary workspace
+        FLIC_CK(h, cudaMalloc(&h->gtab, size_t(N + 1) * (N + 1) * (N + 1) * sizeof(T)));
+        void* greal = nullptr;
+        void* gspec = nullptr;
+        cudaError_t e = cudaMalloc(&greal, size_t(L) * L * L * sizeof(T));
+        if (e == cudaSuccess) e = cudaMalloc(&gspec, size_t(L) * L * (L / 2 + 1) * sizeof(C));
+        if (e == cudaSuccess)
+            e = green_init<T>(N, h->h, h->d.G, reinterpret_cast<T*>(h->gtab), reinterpret_cast<T*>(greal), gspec,
+                              h->tw, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (greal) cudaFree(greal);
+        if (gspec) cudaFree(gspec);
         FLIC_CK(h, e);
     }
     FLIC_CK(h, cudaMalloc(&h->scal, S_COUNT * sizeof(double)));
@@ -270,12 +295,13 @@ int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out) 
         return FLIC_ERR_INVALID_ARG;
     }
     if (desc->precision != FLIC_FP64 && desc->precision != FLIC_MIXED) { g_init_err = "unknown precision"; return FLIC_ERR_INVALID_ARG; }
-    if (desc->poisson_bc != FLIC_PERIODIC) { g_init_err = "only FLIC_PERIODIC is implemented"; return FLIC_ERR_INVALID_ARG; }
+    if (desc->poisson_bc != FLIC_PERIODIC && desc->poisson_bc != FLIC_ISOLATED) { g_init_err = "unknown Poisson boundary"; return FLIC_ERR_INVALID_ARG; }
     flic_handle* h = new flic_handle();
     h->d = *desc;
     h->N = desc->n;
     h->h = (desc->box_max - desc->box_min) / desc->n;
     h->fp64 = desc->precision == FLIC_FP64;
+    h->iso = desc->poisson_bc == FLIC_ISOLATED;
     if (stream) {
         h->st = reinterpret_cast<cudaStream_t>(stream);
     } else {

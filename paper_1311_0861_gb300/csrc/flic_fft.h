@@ -34,4 +34,18 @@ cudaError_t poisson_periodic(const T* rho, const T* nd, T* phi, void* spec, int 
                              const void* tw, int tw_len, const T* asin2, double coef_G_h2,
                              cudaStream_t st);
 
+// Isolated (zero-padded, L = 2N) solve.  gtab: (N+1)^3 reals (the scaled
+// transform of the Green's function, from green_init); spec: N * 2N * (N+1)
+// complex workspace; tw: table of length 2N.  green_init needs (2N)^3 reals
+// (greal) and (2N)^2 (N+1) complex (tmp_spec) of temporary workspace.
+int fft_iso_supported(int N);
+template <typename T>
+cudaError_t fft_prepare_iso(int N);
+template <typename T>
+cudaError_t green_init(int N, double h, double G, T* gtab, T* greal, void* tmp_spec, const void* tw,
+                       cudaStream_t st);
+template <typename T>
+cudaError_t poisson_isolated(const T* rho, const T* nd, T* phi, void* spec, int N, const void* tw, const T* gtab,
+                             cudaStream_t st);
+
 }  // namespace flic

@@ -1,0 +1,349 @@
+// Shared-memory FFT kernels of the Poisson solve (Sec. 2.3), generic in the
+// transform length L and the physical extent P of each axis:
+//   periodic solve: P = L = N;
+//   isolated solve: L = 2N, P = N -- the source is zero-padded to (2N)^3; the
+//   padding is never stored (rows and planes beyond P load as zeros and are
+//   never written back).
+//
+// Each pass is one HBM read and one write of the spectrum.  In-block transforms
+// are Stockham autosort with radix-4, then 2, then 3 butterflies; the radix
+// sequence, strides and index arithmetic are compile-time; twiddles are staged
+// in shared memory from a table exp(-2 pi i j / L), j < L.
+//
+// Spectrum layout: S[z][y][kx], z < P (only physical z planes are ever held),
+// y < L, kx < L/2 + 1 (kx fastest).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "flic_common.cuh"
+
+namespace flic {
+
+template <typename T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+
+// ---------------------------------------------------------------------------
+// r-point DFTs (forward: exp(-2 pi i / r); inverse: conjugate)
+// ---------------------------------------------------------------------------
+template <typename C, bool INV, int R> struct Butterfly;
+template <typename C, bool INV> struct Butterfly<C, INV, 2> {
+    static __device__ __forceinline__ void run(C* x) {
+        C a = x[0];
+        x[0] = cadd(a, x[1]);
+        x[1] = csub(a, x[1]);
+    }
+};
+template <typename C, bool INV> struct Butterfly<C, INV, 4> {
+    static __device__ __forceinline__ void run(C* x) {
+        C a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+        C c = cadd(x[1], x[3]), d0 = csub(x[1], x[3]);
+        C d;   // (x1 - x3) * (-i) forward, * (+i) inverse
+        if (INV) { d.x = -d0.y; d.y = d0.x; } else { d.x = d0.y; d.y = -d0.x; }
+        x[0] = cadd(a, c);
+        x[1] = cadd(b, d);
+        x[2] = csub(a, c);
+        x[3] = csub(b, d);
+    }
+};
+template <typename C, bool INV> struct Butterfly<C, INV, 3> {
+    static __device__ __forceinline__ void run(C* x) {
+        typedef decltype(C().x) R;
+        const R h = R(0.86602540378443864676372317075294);   // sqrt(3)/2
+        C sum = cadd(x[1], x[2]);
+        C dif = csub(x[1], x[2]);
+        C t1;
+        t1.x = x[0].x - R(0.5) * sum.x;
+        t1.y = x[0].y - R(0.5) * sum.y;
+        C t2;   // -i h dif forward, +i h dif inverse
+        if (INV) { t2.x = -h * dif.y; t2.y = h * dif.x; } else { t2.x = h * dif.y; t2.y = -h * dif.x; }
+        x[0] = cadd(x[0], sum);
+        x[1] = cadd(t1, t2);
+        x[2] = csub(t1, t2);
+    }
+};
+
+template <int L> struct FirstRadix {
+    static constexpr int value = (L % 4 == 0) ? 4 : (L % 2 == 0) ? 2 : (L % 3 == 0) ? 3 : 1;
+};
+
+// One Stockham pass of radix R at span NS over NL lines of length L held in
+// shared memory; element (line l, index j) at buf[j * SJ + l * SL].  Twiddle
+// exp(-2 pi i m / TWL) is tw[m] (TWL a multiple of L).
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int R, int TWL>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ A, C* __restrict__ B, const C* tw) {
+    constexpr int NB = L / R;
+    constexpr int TOTAL = NB * NL;
+    constexpr int TSC = (TWL / L) * (L / (NS * R));
+    for (int t = threadIdx.x; t < TOTAL; t += blockDim.x) {
+        const int l = LFAST ? t % NL : t / NB;
+        const int j = LFAST ? t / NL : t % NB;
+        const int k = j % NS;
+        C x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = A[(j + q * NB) * SJ + l * SL];
+        if (NS > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C w = tw[q * k * TSC];
+                if (INV) w.y = -w.y;
+                x[q] = cmul(x[q], w);
+            }
+        }
+        Butterfly<C, INV, R>::run(x);
+        const int idx = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) B[(idx + q * NS) * SJ + l * SL] = x[q];
+    }
+}
+
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int REM, int TWL>
+struct Stockham {
+    static __device__ __forceinline__ C* run(C* A, C* B, const C* tw) {
+        constexpr int R = FirstRadix<REM>::value;
+        static_assert(R > 1, "transform length must be 2^a 3^b");
+        stockham_pass<C, INV, L, NL, SJ, SL, LFAST, NS, R, TWL>(A, B, tw);
+        __syncthreads();
+        return Stockham<C, INV, L, NL, SJ, SL, LFAST, NS * R, REM / R, TWL>::run(B, A, tw);
+    }
+};
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int TWL>
+struct Stockham<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL> {
+    static __device__ __forceinline__ C* run(C* A, C*, const C*) { return A; }
+};
+
+// Block sizes: rows per block of the x passes (~16 KB of complex data per
+// buffer), columns per block of the y/z passes (two L x KB buffers in 96 KB).
+template <typename T, int L> struct FftGeom {
+    typedef typename C2<T>::t C;
+    static constexpr int M = L / 2, MH = M + 1;
+    static constexpr int RB0 = int(16384 / (sizeof(C) * M));
+    static constexpr int RB = RB0 < 1 ? 1 : (RB0 > 64 ? 64 : RB0);
+    static constexpr int KLIM = int(98304 / (2 * sizeof(C) * L));
+    static constexpr int KB = KLIM >= 16 ? 16 : KLIM >= 8 ? 8 : KLIM >= 4 ? 4 : KLIM >= 2 ? 2 : 1;
+    static constexpr size_t smem_x = (size_t(2) * RB * M + L) * sizeof(C);
+    static constexpr size_t smem_c = (size_t(2) * L * KB + L) * sizeof(C);
+};
+
+template <typename C, int L>
+__device__ __forceinline__ void stage_twiddles(C* tws, const C* __restrict__ tw) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = tw[i];
+}
+
+// ---------------------------------------------------------------------------
+// X pass, forward: physical rows (y, z < P) of s = a + b (b may be null),
+// zero-padded to L, packed as L/2 complex values, transformed, unpacked to
+// L/2 + 1 modes.
+// ---------------------------------------------------------------------------
+template <typename T, int L, int P>
+__global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, const T* __restrict__ b,
+                                                     typename C2<T>::t* __restrict__ spec, int nrows,
+                                                     const typename C2<T>::t* __restrict__ tw) {
+    typedef typename C2<T>::t C;
+    typedef FftGeom<T, L> Gm;
+    constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB;
+    static_assert(P % 2 == 0 && P <= L, "physical extent");
+    extern __shared__ __align__(16) unsigned char sm[];
+    C* A = reinterpret_cast<C*>(sm);
+    C* B = A + RB * M;
+    C* tws = B + RB * M;
+    stage_twiddles<C, L>(tws, tw);
+    const int row0 = blockIdx.x * RB;
+    for (int t = threadIdx.x; t < RB * M; t += blockDim.x) {
+        const int l = t / M, j = t % M;
+        const int row = row0 + l;
+        C z;
+        z.x = T(0);
+        z.y = T(0);
+        if (row < nrows && 2 * j < P) {
+            const size_t g = size_t(row) * P + 2 * j;
+            z.x = a[g];
+            z.y = a[g + 1];
+            if (b) {
+                z.x += b[g];
+                z.y += b[g + 1];
+            }
+        }
+        A[l * M + j] = z;
+    }
+    __syncthreads();
+    C* Z = Stockham<C, false, M, RB, 1, M, false, 1, M, L>::run(A, B, tws);
+    for (int t = threadIdx.x; t < RB * MH; t += blockDim.x) {
+        const int l = t / MH, k = t % MH;
+        const int row = row0 + l;
+        if (row >= nrows) continue;
+        C zk = Z[l * M + (k == M ? 0 : k)];
+        C zm = cconj(Z[l * M + (k == 0 ? 0 : M - k)]);
+        C Ek, Ok;
+        Ek.x = T(0.5) * (zk.x + zm.x);
+        Ek.y = T(0.5) * (zk.y + zm.y);
+        Ok.x = T(0.5) * (zk.y - zm.y);     // (zk - zm) / (2 i)
+        Ok.y = -T(0.5) * (zk.x - zm.x);
+        const size_t srow = size_t(row / P) * L + row % P;
+        spec[srow * MH + k] = cadd(Ek, cmul(tws[k], Ok));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// X pass, inverse: L/2 + 1 modes per physical row -> the first P reals
+// ---------------------------------------------------------------------------
+template <typename T, int L, int P>
+__global__ void __launch_bounds__(256) fft_x_inverse(const typename C2<T>::t* __restrict__ spec,
+                                                     T* __restrict__ phi, int nrows,
+                                                     const typename C2<T>::t* __restrict__ tw) {
+    typedef typename C2<T>::t C;
+    typedef FftGeom<T, L> Gm;
+    constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB;
+    extern __shared__ __align__(16) unsigned char sm[];
+    C* A = reinterpret_cast<C*>(sm);
+    C* B = A + RB * M;
+    C* tws = B + RB * M;
+    stage_twiddles<C, L>(tws, tw);
+    __syncthreads();
+    const int row0 = blockIdx.x * RB;
+    for (int t = threadIdx.x; t < RB * M; t += blockDim.x) {
+        const int l = t / M, k = t % M;
+        const int row = row0 + l;
+        C z;
+        if (row < nrows) {
+            const size_t srow = size_t(row / P) * L + row % P;
+            C xk = spec[srow * MH + k];
+            C xm = cconj(spec[srow * MH + (M - k)]);
+            C Ek, D;
+            Ek.x = T(0.5) * (xk.x + xm.x);
+            Ek.y = T(0.5) * (xk.y + xm.y);
+            D.x = T(0.5) * (xk.x - xm.x);
+            D.y = T(0.5) * (xk.y - xm.y);
+            C Ok = cmul(D, cconj(tws[k]));
+            z.x = Ek.x - Ok.y;   // E + i O
+            z.y = Ek.y + Ok.x;
+        } else {
+            z.x = T(0); z.y = T(0);
+        }
+        A[l * M + k] = z;
+    }
+    __syncthreads();
+    C* Z = Stockham<C, true, M, RB, 1, M, false, 1, M, L>::run(A, B, tws);
+    for (int t = threadIdx.x; t < RB * M; t += blockDim.x) {
+        const int l = t / M, j = t % M;
+        const int row = row0 + l;
+        if (row >= nrows || 2 * j >= P) continue;
+        C z = Z[l * M + j];
+        const size_t g = size_t(row) * P + 2 * j;
+        phi[g] = z.x;
+        phi[g + 1] = z.y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Y pass: columns along y for a fixed z < P (forward: P inputs, L outputs;
+// inverse: L inputs, P outputs)
+// ---------------------------------------------------------------------------
+template <typename T, int L, int P, bool INV>
+__global__ void __launch_bounds__(256) fft_y(typename C2<T>::t* __restrict__ spec,
+                                             const typename C2<T>::t* __restrict__ tw) {
+    typedef typename C2<T>::t C;
+    typedef FftGeom<T, L> Gm;
+    constexpr int MH = Gm::MH, KB = Gm::KB;
+    constexpr int NIN = INV ? L : P, NOUT = INV ? P : L;
+    extern __shared__ __align__(16) unsigned char sm[];
+    C* A = reinterpret_cast<C*>(sm);
+    C* B = A + L * KB;
+    C* tws = B + L * KB;
+    stage_twiddles<C, L>(tws, tw);
+    const int k0 = blockIdx.x * KB;
+    const size_t base = size_t(blockIdx.y) * L * MH;
+    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+        const int c = t % KB, y = t / KB;
+        C v;
+        if (k0 + c < MH && y < NIN) v = spec[base + size_t(y) * MH + k0 + c];
+        else { v.x = T(0); v.y = T(0); }
+        A[y * KB + c] = v;
+    }
+    __syncthreads();
+    C* R = Stockham<C, INV, L, KB, KB, 1, true, 1, L, L>::run(A, B, tws);
+    for (int t = threadIdx.x; t < NOUT * KB; t += blockDim.x) {
+        const int c = t % KB, y = t / KB;
+        if (k0 + c < MH) spec[base + size_t(y) * MH + k0 + c] = R[y * KB + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Z pass with the kernel of the solve: forward along z (P inputs), multiply,
+// inverse (P outputs).  ISO = false: the 27-point symbol of Sec. 2.3 with
+// asin2[k] = 2/3 sin^2(pi k / L) and coef = -4 pi G h^2 * scale; ISO = true:
+// the precomputed transform of the isolated Green's function, stored by its
+// even symmetry as gtab[kz'][ky'][kx], kz' = min(kz, L - kz), ky' likewise.
+// ---------------------------------------------------------------------------
+template <typename T, int L, int P, bool ISO>
+__global__ void __launch_bounds__(256) fft_z_solve(typename C2<T>::t* __restrict__ spec,
+                                                   const typename C2<T>::t* __restrict__ tw,
+                                                   const T* __restrict__ asin2, T coef,
+                                                   const T* __restrict__ gtab) {
+    typedef typename C2<T>::t C;
+    typedef FftGeom<T, L> Gm;
+    constexpr int MH = Gm::MH, KB = Gm::KB;
+    extern __shared__ __align__(16) unsigned char sm[];
+    C* A = reinterpret_cast<C*>(sm);
+    C* B = A + L * KB;
+    C* tws = B + L * KB;
+    stage_twiddles<C, L>(tws, tw);
+    const int k0 = blockIdx.x * KB;
+    const int y = blockIdx.y;
+    constexpr size_t zs = size_t(L) * MH;
+    const size_t base = size_t(y) * MH;
+    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+        const int c = t % KB, z = t / KB;
+        C v;
+        if (k0 + c < MH && z < P) v = spec[base + size_t(z) * zs + k0 + c];
+        else { v.x = T(0); v.y = T(0); }
+        A[z * KB + c] = v;
+    }
+    __syncthreads();
+    C* R = Stockham<C, false, L, KB, KB, 1, true, 1, L, L>::run(A, B, tws);
+    C* S = (R == A) ? B : A;
+    const int ys = y <= L / 2 ? y : L - y;
+    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+        const int c = t % KB, z = t / KB;
+        const int kx = k0 + c;
+        C v = R[z * KB + c];
+        if (kx < MH) {
+            T g;
+            if (ISO) {
+                const int zz = z <= L / 2 ? z : L - z;
+                g = gtab[(size_t(zz) * (L / 2 + 1) + ys) * MH + kx];
+            } else {
+                const T ax = asin2[kx], ay = asin2[y], az = asin2[z];
+                // 1 - f_x f_y f_z without cancellation, f = 1 - a
+                const T D = T(6) * (ax + (T(1) - ax) * (ay + (T(1) - ay) * az));
+                g = (kx == 0 && y == 0 && z == 0) ? T(0) : coef / D;
+            }
+            v.x *= g;
+            v.y *= g;
+        }
+        S[z * KB + c] = v;
+    }
+    __syncthreads();
+    C* Q = Stockham<C, true, L, KB, KB, 1, true, 1, L, L>::run(S, R, tws);
+    for (int t = threadIdx.x; t < P * KB; t += blockDim.x) {
+        const int c = t % KB, z = t / KB;
+        if (k0 + c < MH) spec[base + size_t(z) * zs + k0 + c] = Q[z * KB + c];
+    }
+}
+
+}  // namespace flic

@@ -203,3 +203,32 @@ def test_invalid_arguments(flic):
     assert ei.value.code == flic.ERR_INVALID_ARG
     with pytest.raises(flic.FlicError):
         flic.Grid(16, gamma=1.0)
+
+
+@pytest.mark.parametrize("N,precision,tol", [(8, "fp64", 1e-12), (12, "fp64", 1e-12), (24, "fp64", 1e-12),
+                                             (32, "fp64", 1e-12), (48, "mixed", 2e-5), (64, "mixed", 2e-5)])
+def test_poisson_isolated(flic, N, precision, tol):
+    """Zero-padded solve vs the oracle's (pinned to a direct O(N^6) sum)."""
+    s = I.random_state((N, N, N), seed=60 + N)
+    prm = O.Params(h=s.h, poisson="isolated")
+    ref = O.solve_poisson(s.state, prm)
+    with flic.Grid(N, precision=precision, poisson="isolated", box=(-1.0, -1.0 + s.h * N)) as g:
+        g.set_state(s.state)
+        phi = g.solve_poisson()
+    assert np.max(np.abs(phi - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N", [16, 24])
+def test_steps_isolated_fp64(flic, N):
+    s = I.random_state((N, N, N), seed=70 + N)
+    prm = O.Params(h=s.h, gamma=s.gamma, poisson="isolated")
+    ref, rrec = O.run(s.state, prm, 3)
+    with flic.Grid(N, precision="fp64", poisson="isolated", box=(-1.0, -1.0 + s.h * N)) as g:
+        g.set_state(s.state)
+        for _ in range(3):
+            g.step()
+        out = g.get_state()
+        d = g.step_diagnostics()
+    err = rel_l1(out, ref)
+    assert max(err.values()) <= 1e-10, err
+    assert abs(d["epot"] - rrec[-1]["epot"]) <= 1e-11 * abs(rrec[-1]["epot"])
