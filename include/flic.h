@@ -178,6 +178,31 @@ int flic_diagnostics(flic_handle* h, flic_diag* out);
 int flic_state_diagnostics_noalloc(const double* const fields[FLIC_NFIELDS], const double* phi, int n, double h,
                                    double gamma, void* stream, flic_diag* out);
 
+/* ---- batched ensembles (independent runs, uneven sizes, advanced together) ----
+ *
+ * nruns grids, descs[r] for run r; every constant except n must be equal across
+ * runs (n = 2^a 3^b, multiple of 4, 8..512).  Each step solves every run's
+ * Poisson equation (one set of FFT launches per grid size, batched over the runs
+ * of that size), then runs each fluid stage as ONE launch over a work list that
+ * spans all runs' tiles, and the setup / reduction as one launch each; steps are
+ * replayed as CUDA graphs.  Each run keeps its own CFL step (tau from its own
+ * signal speed), diagnostics record and status.  Errors of create: message in
+ * flic_last_error(NULL); afterwards flic_ensemble_last_error(e). */
+typedef struct flic_ensemble flic_ensemble;
+int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, flic_ensemble** out);
+int flic_ensemble_set_state(flic_ensemble* e, int run, const double* const fields[FLIC_NFIELDS]);  /* host */
+int flic_ensemble_get_state(flic_ensemble* e, int run, double* const fields[FLIC_NFIELDS]);        /* host */
+/* nsteps steps of every run (dt > 0: fixed step for all; dt <= 0: each run's CFL
+ * step); waits and checks every run's status only if `sync`. */
+int flic_ensemble_step(flic_ensemble* e, int nsteps, double dt, int sync);
+/* Last step record of one run (same fields as flic_step_diagnostics). */
+int flic_ensemble_diagnostics(flic_ensemble* e, int run, flic_diag* out);
+/* nsteps steps timed with CUDA events on the ensemble's stream. */
+int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double* total_ms);
+int flic_ensemble_launches_per_step(flic_ensemble* e);
+int flic_ensemble_destroy(flic_ensemble* e);
+const char* flic_ensemble_last_error(flic_ensemble* e);
+
 /* Waits for all work of the handle. */
 int flic_sync(flic_handle* h);
 

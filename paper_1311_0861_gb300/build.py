@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflic.so")
-SOURCES = ["flic_api.cu", "flic_stencil.cu", "flic_fft.cu", "flic_fft_iso.cu", "flic_util.cu", "flic_noalloc.cu"]
+SOURCES = ["flic_api.cu", "flic_stencil.cu", "flic_fft.cu", "flic_fft_iso.cu", "flic_util.cu", "flic_noalloc.cu", "flic_ensemble.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xptxas", "-v"]

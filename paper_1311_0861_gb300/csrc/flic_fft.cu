@@ -43,7 +43,8 @@ static cudaError_t prepare_n() {
 
 template <typename T, int N>
 static cudaError_t solve_n(const T* rho, const T* nd, T* phi, void* spec_v, const void* tw_v, const T* asin2,
-                           double coef_G_h2, cudaStream_t st) {
+                           double coef_G_h2, cudaStream_t st, int nb, size_t bs_in, size_t bs_phi,
+                           size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, N> Gm;
     C* spec = reinterpret_cast<C*>(spec_v);
@@ -53,11 +54,12 @@ static cudaError_t solve_n(const T* rho, const T* nd, T* phi, void* spec_v, cons
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
     // total scale of the unnormalised inverse: 1 / ((N/2) N N)
     const double coef = -4.0 * 3.14159265358979323846 * coef_G_h2 / (double(Gm::M) * N * N);
-    fft_x_forward<T, N, N><<<gx, 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw);
-    fft_y<T, N, N, false><<<dim3(gk, N), 256, Gm::smem_c, st>>>(spec, tw);
-    fft_z_solve<T, N, N, false><<<dim3(gk, N), 256, Gm::smem_c, st>>>(spec, tw, asin2, T(coef), nullptr);
-    fft_y<T, N, N, true><<<dim3(gk, N), 256, Gm::smem_c, st>>>(spec, tw);
-    fft_x_inverse<T, N, N><<<gx, 256, Gm::smem_x, st>>>(spec, phi, nrows, tw);
+    fft_x_forward<T, N, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
+    fft_y<T, N, N, false><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, bs_spec);
+    fft_z_solve<T, N, N, false><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, asin2, T(coef), nullptr,
+                                                                          bs_spec);
+    fft_y<T, N, N, true><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, bs_spec);
+    fft_x_inverse<T, N, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
     return cudaGetLastError();
 }
 
@@ -73,10 +75,12 @@ cudaError_t fft_prepare(int N) {
 
 template <typename T>
 cudaError_t poisson_periodic(const T* rho, const T* nd, T* phi, void* spec, int N, const FftPlans&,
-                             const void* tw, int tw_len, const T* asin2, double coef_G_h2, cudaStream_t st) {
-    if (tw_len != N) return cudaErrorInvalidValue;
+                             const void* tw, int tw_len, const T* asin2, double coef_G_h2, cudaStream_t st,
+                             int nbatch, size_t bs_in, size_t bs_phi, size_t bs_spec) {
+    if (tw_len != N || nbatch < 1) return cudaErrorInvalidValue;
     switch (N) {
-#define FLIC_CASE(n) case n: return solve_n<T, n>(rho, nd, phi, spec, tw, asin2, coef_G_h2, st);
+#define FLIC_CASE(n) \
+    case n: return solve_n<T, n>(rho, nd, phi, spec, tw, asin2, coef_G_h2, st, nbatch, bs_in, bs_phi, bs_spec);
         FLIC_FFT_SIZES(FLIC_CASE)
 #undef FLIC_CASE
         default: return cudaErrorInvalidValue;
@@ -86,9 +90,10 @@ cudaError_t poisson_periodic(const T* rho, const T* nd, T* phi, void* spec, int 
 template cudaError_t fft_prepare<float>(int);
 template cudaError_t fft_prepare<double>(int);
 template cudaError_t poisson_periodic<float>(const float*, const float*, float*, void*, int, const FftPlans&,
-                                             const void*, int, const float*, double, cudaStream_t);
+                                             const void*, int, const float*, double, cudaStream_t, int, size_t,
+                                             size_t, size_t);
 template cudaError_t poisson_periodic<double>(const double*, const double*, double*, void*, int,
                                               const FftPlans&, const void*, int, const double*, double,
-                                              cudaStream_t);
+                                              cudaStream_t, int, size_t, size_t, size_t);
 
 }  // namespace flic

@@ -29,10 +29,14 @@ cudaError_t fft_prepare(int N);
 //   spec: (N/2+1) N N complex workspace; tw: table exp(-2 pi i j / tw_len),
 //   j < tw_len (tw_len a multiple of N); asin2[k] = 2/3 sin^2(pi k / N), k < N;
 //   coef_G_h2 = G h^2.
+//   nbatch independent runs of the same N in one set of launches: run r reads
+//   rho + r*bs_in, nd + r*bs_in, writes phi + r*bs_phi, uses spec + r*bs_spec
+//   (complex elements).
 template <typename T>
 cudaError_t poisson_periodic(const T* rho, const T* nd, T* phi, void* spec, int N, const FftPlans& pl,
                              const void* tw, int tw_len, const T* asin2, double coef_G_h2,
-                             cudaStream_t st);
+                             cudaStream_t st, int nbatch = 1, size_t bs_in = 0, size_t bs_phi = 0,
+                             size_t bs_spec = 0);
 
 // Isolated (zero-padded, L = 2N) solve.  gtab: (N+1)^3 reals (the scaled
 // transform of the Green's function, from green_init); spec: N * 2N * (N+1)
@@ -46,6 +50,7 @@ cudaError_t green_init(int N, double h, double G, T* gtab, T* greal, void* tmp_s
                        cudaStream_t st);
 template <typename T>
 cudaError_t poisson_isolated(const T* rho, const T* nd, T* phi, void* spec, int N, const void* tw, const T* gtab,
-                             cudaStream_t st);
+                             cudaStream_t st, int nbatch = 1, size_t bs_in = 0, size_t bs_phi = 0,
+                             size_t bs_spec = 0);
 
 }  // namespace flic

@@ -95,8 +95,8 @@ static cudaError_t green_init_n(double h, double G, T* gtab, T* greal, void* tmp
     const int nrows = L * L;
     const int gx = (nrows + Gm::RB - 1) / Gm::RB;
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
-    fft_x_forward<T, L, L><<<gx, 256, Gm::smem_x, st>>>(greal, nullptr, spec, nrows, tw);
-    fft_y<T, L, L, false><<<dim3(gk, L), 256, Gm::smem_c, st>>>(spec, tw);
+    fft_x_forward<T, L, L><<<gx, 256, Gm::smem_x, st>>>(greal, nullptr, spec, nrows, tw, 0, 0);
+    fft_y<T, L, L, false><<<dim3(gk, L), 256, Gm::smem_c, st>>>(spec, tw, 0);
     const double scale = 1.0 / (double(L / 2) * L * L);
     fft_z_green<T, L><<<dim3(gk, L / 2 + 1), 256, Gm::smem_c, st>>>(spec, tw, T(scale), gtab);
     return cudaGetLastError();
@@ -104,7 +104,7 @@ static cudaError_t green_init_n(double h, double G, T* gtab, T* greal, void* tmp
 
 template <typename T, int N>
 static cudaError_t solve_iso_n(const T* rho, const T* nd, T* phi, void* spec_v, const void* tw_v, const T* gtab,
-                               cudaStream_t st) {
+                               cudaStream_t st, int nb, size_t bs_in, size_t bs_phi, size_t bs_spec) {
     constexpr int L = 2 * N;
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
@@ -113,11 +113,11 @@ static cudaError_t solve_iso_n(const T* rho, const T* nd, T* phi, void* spec_v, 
     const int nrows = N * N;
     const int gx = (nrows + Gm::RB - 1) / Gm::RB;
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
-    fft_x_forward<T, L, N><<<gx, 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw);
-    fft_y<T, L, N, false><<<dim3(gk, N), 256, Gm::smem_c, st>>>(spec, tw);
-    fft_z_solve<T, L, N, true><<<dim3(gk, L), 256, Gm::smem_c, st>>>(spec, tw, nullptr, T(0), gtab);
-    fft_y<T, L, N, true><<<dim3(gk, N), 256, Gm::smem_c, st>>>(spec, tw);
-    fft_x_inverse<T, L, N><<<gx, 256, Gm::smem_x, st>>>(spec, phi, nrows, tw);
+    fft_x_forward<T, L, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
+    fft_y<T, L, N, false><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, bs_spec);
+    fft_z_solve<T, L, N, true><<<dim3(gk, L, nb), 256, Gm::smem_c, st>>>(spec, tw, nullptr, T(0), gtab, bs_spec);
+    fft_y<T, L, N, true><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, bs_spec);
+    fft_x_inverse<T, L, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
     return cudaGetLastError();
 }
 
@@ -155,9 +155,10 @@ cudaError_t green_init(int N, double h, double G, T* gtab, T* greal, void* tmp_s
 
 template <typename T>
 cudaError_t poisson_isolated(const T* rho, const T* nd, T* phi, void* spec, int N, const void* tw, const T* gtab,
-                             cudaStream_t st) {
+                             cudaStream_t st, int nbatch, size_t bs_in, size_t bs_phi, size_t bs_spec) {
+    if (nbatch < 1) return cudaErrorInvalidValue;
     switch (N) {
-#define FLIC_CASE(n) case n: return solve_iso_n<T, n>(rho, nd, phi, spec, tw, gtab, st);
+#define FLIC_CASE(n) case n: return solve_iso_n<T, n>(rho, nd, phi, spec, tw, gtab, st, nbatch, bs_in, bs_phi, bs_spec);
         FLIC_ISO_SIZES(FLIC_CASE)
 #undef FLIC_CASE
         default: return cudaErrorInvalidValue;
@@ -169,8 +170,8 @@ template cudaError_t fft_prepare_iso<double>(int);
 template cudaError_t green_init<float>(int, double, double, float*, float*, void*, const void*, cudaStream_t);
 template cudaError_t green_init<double>(int, double, double, double*, double*, void*, const void*, cudaStream_t);
 template cudaError_t poisson_isolated<float>(const float*, const float*, float*, void*, int, const void*,
-                                             const float*, cudaStream_t);
+                                             const float*, cudaStream_t, int, size_t, size_t, size_t);
 template cudaError_t poisson_isolated<double>(const double*, const double*, double*, void*, int, const void*,
-                                              const double*, cudaStream_t);
+                                              const double*, cudaStream_t, int, size_t, size_t, size_t);
 
 }  // namespace flic

@@ -153,11 +153,16 @@ __device__ __forceinline__ void stage_twiddles(C* tws, const C* __restrict__ tw)
 template <typename T, int L, int P>
 __global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, const T* __restrict__ b,
                                                      typename C2<T>::t* __restrict__ spec, int nrows,
-                                                     const typename C2<T>::t* __restrict__ tw) {
+                                                     const typename C2<T>::t* __restrict__ tw, size_t bs_in,
+                                                     size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
     constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB;
     static_assert(P % 2 == 0 && P <= L, "physical extent");
+    // batch of independent runs along grid y
+    a += blockIdx.y * bs_in;
+    if (b) b += blockIdx.y * bs_in;
+    spec += blockIdx.y * bs_spec;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
     C* B = A + RB * M;
@@ -205,10 +210,13 @@ __global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, co
 template <typename T, int L, int P>
 __global__ void __launch_bounds__(256) fft_x_inverse(const typename C2<T>::t* __restrict__ spec,
                                                      T* __restrict__ phi, int nrows,
-                                                     const typename C2<T>::t* __restrict__ tw) {
+                                                     const typename C2<T>::t* __restrict__ tw, size_t bs_spec,
+                                                     size_t bs_phi) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
     constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB;
+    spec += blockIdx.y * bs_spec;
+    phi += blockIdx.y * bs_phi;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
     C* B = A + RB * M;
@@ -256,11 +264,12 @@ __global__ void __launch_bounds__(256) fft_x_inverse(const typename C2<T>::t* __
 // ---------------------------------------------------------------------------
 template <typename T, int L, int P, bool INV>
 __global__ void __launch_bounds__(256) fft_y(typename C2<T>::t* __restrict__ spec,
-                                             const typename C2<T>::t* __restrict__ tw) {
+                                             const typename C2<T>::t* __restrict__ tw, size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
     constexpr int MH = Gm::MH, KB = Gm::KB;
     constexpr int NIN = INV ? L : P, NOUT = INV ? P : L;
+    spec += blockIdx.z * bs_spec;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
     C* B = A + L * KB;
@@ -294,10 +303,11 @@ template <typename T, int L, int P, bool ISO>
 __global__ void __launch_bounds__(256) fft_z_solve(typename C2<T>::t* __restrict__ spec,
                                                    const typename C2<T>::t* __restrict__ tw,
                                                    const T* __restrict__ asin2, T coef,
-                                                   const T* __restrict__ gtab) {
+                                                   const T* __restrict__ gtab, size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
     constexpr int MH = Gm::MH, KB = Gm::KB;
+    spec += blockIdx.z * bs_spec;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
     C* B = A + L * KB;

@@ -24,6 +24,11 @@ template <typename T> StepCfg gas_cfg(int N, int tz);
 template <typename T> StepCfg bme_cfg(int N, int tz);
 template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
 template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
+// One launch over a work list spanning several runs (table and work in device memory).
+template <typename T>
+cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st);
 
 // float64 <-> storage precision conversion of one field.
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);
@@ -52,6 +57,29 @@ enum Scalar { S_VMAX_CUR = 0, S_TAU, S_VMAX_NEXT, S_TIME, S_COUNT = 8 };
 
 // tau = dt (dt > 0) or courant*h / vmax_cur; clears vmax_next and the status word.
 cudaError_t step_prep(double* scal, unsigned int* status, double dt, double courant_h, cudaStream_t st);
+
+// Per-run scalars of a batched step.
+struct RunScalars {
+    double* scal;
+    unsigned int* status;
+    double courant_h;
+};
+cudaError_t step_prep_batch(const RunScalars* runs, int nruns, double dt, cudaStream_t st);
+
+// Arguments of the reduction of one run's partial rows (a: gas, b: moments).
+struct FinalizeArgs {
+    const double* pa;
+    int na;
+    const double* pb;
+    int nb;
+    double h3;
+    double* scal;
+    unsigned int* status;
+    flic_diag* diag;
+    double* level1;
+};
+// one two-level reduction per run of the device table
+cudaError_t step_finalize_batch(const FinalizeArgs* table, int nruns, int count_step, cudaStream_t st);
 
 // Sums the per-block partials (fixed order, compensated), writes the record and
 // advances vmax_cur, time and the step counter.  count_step = 0 for a

@@ -64,7 +64,18 @@ cudaError_t prepare() {
 
 template <class P, typename T, int TX, int TY, int MB, bool SX>
 cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-    fluid_step_kernel<P, T, TX, TY, MB, SX><<<dim3(c.tiles_x * c.tiles_y, c.blocks_z), c.threads, c.smem, st>>>(a);
+    BatchArgs<T> none{nullptr, nullptr};
+    fluid_step_kernel<P, T, TX, TY, MB, SX>
+        <<<dim3(c.tiles_x * c.tiles_y, c.blocks_z), c.threads, c.smem, st>>>(a, none);
+    return cudaGetLastError();
+}
+
+template <class P, typename T, int TX, int TY, int MB, bool SX>
+cudaError_t launch_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
+    StencilArgs<T> unused{};
+    BatchArgs<T> b{table, work};
+    fluid_step_kernel<P, T, TX, TY, MB, SX>
+        <<<nwork, TX * TY, Geom<P, T, TX, TY, SX>::smem_bytes, st>>>(unused, b);
     return cudaGetLastError();
 }
 
@@ -82,6 +93,20 @@ template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const Step
 template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
     return launch<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB, Tiles<T>::BS>(a, c, st);
 }
+
+template <typename T>
+cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
+    return launch_batch<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB, false>(table, work, nwork, st);
+}
+template <typename T>
+cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
+    return launch_batch<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB, Tiles<T>::BS>(table, work, nwork,
+                                                                                              st);
+}
+template cudaError_t launch_gas_batch<float>(const StencilArgs<float>*, const WorkItem*, int, cudaStream_t);
+template cudaError_t launch_gas_batch<double>(const StencilArgs<double>*, const WorkItem*, int, cudaStream_t);
+template cudaError_t launch_bme_batch<float>(const StencilArgs<float>*, const WorkItem*, int, cudaStream_t);
+template cudaError_t launch_bme_batch<double>(const StencilArgs<double>*, const WorkItem*, int, cudaStream_t);
 
 template <typename T> cudaError_t stencil_prepare() {
     cudaError_t e = prepare<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB, false>();

@@ -29,6 +29,11 @@
 
 namespace flic {
 
+// Work item of a batched launch: (run, tile, z chunk, partial-sum row of the run).
+struct WorkItem {
+    int run, tile, chunk, prow;
+};
+
 template <typename T>
 struct StencilArgs {
     const T* in;              // input state, field f at in + f * fs (fluid-local field order)
@@ -44,6 +49,14 @@ struct StencilArgs {
     double* partials;         // [num_blocks][Q_COUNT] per-block sums (unscaled by h^3)
     double* vmax;             // signal speed of the output state (atomic max)
     unsigned int* status;     // ST_* bits
+};
+
+// Batched launch: block b processes work[b] with the arguments of table[work[b].run].
+// Both null for a single run (block (x, y) = (tile, chunk) with the kernel argument).
+template <typename T>
+struct BatchArgs {
+    const StencilArgs<T>* table;
+    const WorkItem* work;
 };
 
 // ---------------------------------------------------------------------------
@@ -379,7 +392,7 @@ __device__ __forceinline__ int ring_slot(int p) { return ((p % RING_SLOTS) + RIN
 
 template <class P, typename T, int TX, int TY, int MINB, bool SEX>
 __global__ void __launch_bounds__(TX * TY, MINB)
-fluid_step_kernel(StencilArgs<T> a) {
+fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     using Gm = Geom<P, T, TX, TY, SEX>;
     constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, H2 = Gm::H2, R1 = Gm::R1, W1 = Gm::W1;
     constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE, NEX = P::NEX;
@@ -399,12 +412,25 @@ fluid_step_kernel(StencilArgs<T> a) {
     int* yoff = xoff + CPR;                                            // wrapped y * N of R2 rows
 
     const int tid = threadIdx.x;
+    int tile, chunk, prow;
+    StencilArgs<T> a;
+    if (batch.work) {
+        const WorkItem w = batch.work[blockIdx.x];
+        a = batch.table[w.run];
+        tile = w.tile;
+        chunk = w.chunk;
+        prow = w.prow;
+    } else {
+        a = a1;
+        tile = blockIdx.x;
+        chunk = blockIdx.y;
+        prow = blockIdx.y * gridDim.x + blockIdx.x;
+    }
     const int N = a.n;
     const size_t plane = size_t(N) * N;
-    const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = (tile / a.tiles_x) * TY;
-    const int z0 = blockIdx.y * a.tz;
+    const int z0 = chunk * a.tz;
     const int z1 = min(z0 + a.tz, N);
     const T tau = T(*a.tau);
     const T rat = T(*a.tau * a.inv_h);
@@ -614,7 +640,7 @@ fluid_step_kernel(StencilArgs<T> a) {
             double v = (lane < NW) ? red[lane * (P::NQ + 1) + k] : 0.0;
             if (k < P::NQ) {
                 v = warp_sum(v);
-                if (lane == 0) a.partials[(size_t(blockIdx.y) * gridDim.x + blockIdx.x) * Q_COUNT + P::qslot(k)] = v;
+                if (lane == 0) a.partials[size_t(prow) * Q_COUNT + P::qslot(k)] = v;
             } else {
                 v = warp_max(v);
                 if (lane == 0) atomic_max_nonneg(a.vmax, v);

@@ -132,6 +132,20 @@ cudaError_t step_prep(double* scal, unsigned int* status, double dt, double cour
     return cudaGetLastError();
 }
 
+__global__ void step_prep_batch_kernel(const RunScalars* __restrict__ runs, int nruns, double dt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    const RunScalars a = runs[r];
+    a.scal[S_TAU] = (dt > 0.0) ? dt : a.courant_h / a.scal[S_VMAX_CUR];
+    a.scal[S_VMAX_NEXT] = 0.0;
+    *a.status = 0u;
+}
+
+cudaError_t step_prep_batch(const RunScalars* runs, int nruns, double dt, cudaStream_t st) {
+    step_prep_batch_kernel<<<(nruns + 127) / 128, 128, 0, st>>>(runs, nruns, dt);
+    return cudaGetLastError();
+}
+
 // Deterministic two-level sum of the per-block partials.  Level 1: FIN_BLOCKS
 // blocks each sum a fixed contiguous range of rows (Neumaier compensation) and
 // reduce in a fixed order -- float64 throughput per SM is low on this part, so
@@ -173,24 +187,24 @@ __device__ __forceinline__ void block_sum_rows(const double* __restrict__ pa, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) finalize_level1(const double* __restrict__ pa, int na,
-                                                      const double* __restrict__ pb, int nb, double* level1) {
+__device__ __forceinline__ void finalize_level1_body(const FinalizeArgs& f, int blk, int nblk) {
     __shared__ double res[Q_COUNT];
-    const int rows = na + nb;
-    const int per = (rows + gridDim.x - 1) / gridDim.x;
-    const int r0 = min(rows, int(blockIdx.x) * per), r1 = min(rows, r0 + per);
-    block_sum_rows<256>(pa, na, pb, nb, r0, r1, res);
-    if (threadIdx.x < Q_COUNT) level1[size_t(blockIdx.x) * Q_COUNT + threadIdx.x] = res[threadIdx.x];
+    const int nb = f.pb ? f.nb : 0;
+    const int rows = f.na + nb;
+    const int per = (rows + nblk - 1) / nblk;
+    const int r0 = min(rows, blk * per), r1 = min(rows, r0 + per);
+    block_sum_rows<256>(f.pa, f.na, f.pb, nb, r0, r1, res);
+    if (threadIdx.x < Q_COUNT) f.level1[size_t(blk) * Q_COUNT + threadIdx.x] = res[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(64) step_finalize_kernel(const double* __restrict__ level1, double h3,
-                                                          double* scal, unsigned int* status, flic_diag* d,
-                                                          int count_step) {
+__device__ __forceinline__ void finalize_level2_body(const FinalizeArgs& f, int count_step) {
     __shared__ double res[Q_COUNT];
-    block_sum_rows<64>(level1, FIN_BLOCKS, nullptr, 0, 0, FIN_BLOCKS, res);
-    if (threadIdx.x < Q_COUNT) res[threadIdx.x] *= h3;
+    block_sum_rows<64>(f.level1, FIN_BLOCKS, nullptr, 0, 0, FIN_BLOCKS, res);
+    if (threadIdx.x < Q_COUNT) res[threadIdx.x] *= f.h3;
     __syncthreads();
     if (threadIdx.x == 0) {
+        flic_diag* d = f.diag;
+        double* scal = f.scal;
         d->mass_gas = res[Q_MASS_GAS];
         d->mass_bme = res[Q_MASS_BME];
         d->mom[0] = res[Q_MOMX];
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(64) step_finalize_kernel(const double* __restr
         d->epot = res[Q_EPOT];
         d->kappa_gas = res[Q_KAPPA_GAS];
         d->kappa_bme = res[Q_KAPPA_BME];
-        d->status = (*status & ST_NONPHYSICAL) ? FLIC_ERR_NONPHYSICAL : FLIC_OK;
+        d->status = (*f.status & ST_NONPHYSICAL) ? FLIC_ERR_NONPHYSICAL : FLIC_OK;
         if (count_step) {
             d->vmax = scal[S_VMAX_NEXT];
             d->dt = scal[S_TAU];
@@ -219,10 +233,34 @@ __global__ void __launch_bounds__(64) step_finalize_kernel(const double* __restr
     }
 }
 
+__global__ void __launch_bounds__(256) finalize_level1(FinalizeArgs f) {
+    finalize_level1_body(f, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(64) step_finalize_kernel(FinalizeArgs f, int count_step) {
+    finalize_level2_body(f, count_step);
+}
+// batched: one run per grid row (level 1) / per block (level 2)
+__global__ void __launch_bounds__(256) finalize_level1_batch(const FinalizeArgs* __restrict__ table) {
+    const FinalizeArgs f = table[blockIdx.y];
+    finalize_level1_body(f, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(64) step_finalize_batch_kernel(const FinalizeArgs* __restrict__ table,
+                                                                int count_step) {
+    const FinalizeArgs f = table[blockIdx.x];
+    finalize_level2_body(f, count_step);
+}
+
 cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
                           unsigned int* status, flic_diag* diag, int count_step, double* level1, cudaStream_t st) {
-    finalize_level1<<<FIN_BLOCKS, 256, 0, st>>>(pa, na, pb, pb ? nb : 0, level1);
-    step_finalize_kernel<<<1, 64, 0, st>>>(level1, h3, scal, status, diag, count_step);
+    FinalizeArgs f{pa, na, pb, nb, h3, scal, status, diag, level1};
+    finalize_level1<<<FIN_BLOCKS, 256, 0, st>>>(f);
+    step_finalize_kernel<<<1, 64, 0, st>>>(f, count_step);
+    return cudaGetLastError();
+}
+
+cudaError_t step_finalize_batch(const FinalizeArgs* table, int nruns, int count_step, cudaStream_t st) {
+    finalize_level1_batch<<<dim3(FIN_BLOCKS, nruns), 256, 0, st>>>(table);
+    step_finalize_batch_kernel<<<nruns, 64, 0, st>>>(table, count_step);
     return cudaGetLastError();
 }
 

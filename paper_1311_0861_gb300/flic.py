@@ -31,7 +31,10 @@ EXPORTS = ("flic_init_grid", "flic_set_state", "flic_set_state_device", "flic_ge
            "flic_get_state_device", "flic_step", "flic_run", "flic_solve_poisson",
            "flic_step_diagnostics", "flic_diagnostics", "flic_sync", "flic_destroy",
            "flic_last_error", "flic_version", "flic_profile", "flic_launches_per_step",
-           "flic_state_diagnostics_noalloc")
+           "flic_state_diagnostics_noalloc",
+           "flic_ensemble_create", "flic_ensemble_set_state", "flic_ensemble_get_state", "flic_ensemble_step",
+           "flic_ensemble_diagnostics", "flic_ensemble_profile", "flic_ensemble_launches_per_step",
+           "flic_ensemble_destroy", "flic_ensemble_last_error")
 NSTAGES = 4
 STAGES = ("poisson", "gas", "bme", "finalize")
 
@@ -85,6 +88,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.flic_profile.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double)]
     lib.flic_launches_per_step.argtypes = [P]
+    lib.flic_ensemble_create.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.flic_ensemble_set_state.argtypes = [P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.flic_ensemble_get_state.argtypes = [P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.flic_ensemble_step.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.flic_ensemble_diagnostics.argtypes = [P, ctypes.c_int, ctypes.POINTER(Diag)]
+    lib.flic_ensemble_profile.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.flic_ensemble_launches_per_step.argtypes = [P]
+    lib.flic_ensemble_destroy.argtypes = [P]
+    lib.flic_ensemble_last_error.argtypes = [P]
+    lib.flic_ensemble_last_error.restype = ctypes.c_char_p
     lib.flic_state_diagnostics_noalloc.argtypes = [ctypes.POINTER(P), P, ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_double, P, ctypes.POINTER(Diag)]
     lib.flic_step_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
@@ -95,7 +108,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.flic_last_error.restype = ctypes.c_char_p
     lib.flic_version.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("flic_last_error", "flic_version"):
+        if name not in ("flic_last_error", "flic_version", "flic_ensemble_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -262,6 +275,79 @@ class Grid:
         if getattr(self, "_h", None) and self._h.value:
             self.lib.flic_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent runs of uneven sizes advanced together (a libflic ensemble)."""
+
+    def __init__(self, sizes, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
+                 precision: str = "mixed", poisson: str = "periodic", stream: int = 0):
+        self.lib = load()
+        self.sizes = [int(n) for n in sizes]
+        descs = (GridDesc * len(self.sizes))(*[
+            GridDesc(n, box[0], box[1], gamma, G, courant, eta, {"fp64": FP64, "mixed": MIXED}[precision],
+                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson]) for n in self.sizes])
+        self._e = ctypes.c_void_p()
+        rc = self.lib.flic_ensemble_create(descs, len(self.sizes), ctypes.c_void_p(stream or None),
+                                           ctypes.byref(self._e))
+        if rc != OK:
+            raise FlicError(rc, self.lib.flic_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc < 0:
+            raise FlicError(rc, self.lib.flic_ensemble_last_error(self._e).decode())
+        return rc
+
+    def set_state(self, run: int, state):
+        n = self.sizes[run]
+        arrs = _field_list(state, n)
+        ptrs = []
+        for a in arrs:
+            p, dev = _ptr_of(a, False)
+            if dev:
+                raise FlicError(ERR_INVALID_ARG, "ensemble states are host arrays")
+            ptrs.append(p)
+        self._check(self.lib.flic_ensemble_set_state(self._e, run, (ctypes.c_void_p * NFIELDS)(*ptrs)))
+
+    def get_state(self, run: int) -> dict:
+        n = self.sizes[run]
+        res = {f: np.empty((n, n, n)) for f in FIELDS}
+        ptrs = (ctypes.c_void_p * NFIELDS)(*[res[f].ctypes.data for f in FIELDS])
+        self._check(self.lib.flic_ensemble_get_state(self._e, run, ptrs))
+        return res
+
+    def step(self, nsteps: int = 1, dt: float = 0.0, sync: bool = True):
+        self._check(self.lib.flic_ensemble_step(self._e, int(nsteps), dt, int(bool(sync))))
+
+    def diagnostics(self, run: int) -> dict:
+        d = Diag()
+        self._check(self.lib.flic_ensemble_diagnostics(self._e, run, ctypes.byref(d)))
+        return d.as_dict()
+
+    def profile(self, nsteps: int, dt: float = 0.0) -> float:
+        ms = ctypes.c_double()
+        self._check(self.lib.flic_ensemble_profile(self._e, int(nsteps), dt, ctypes.byref(ms)))
+        return ms.value
+
+    def launches_per_step(self) -> int:
+        return self._check(self.lib.flic_ensemble_launches_per_step(self._e))
+
+    def close(self):
+        if getattr(self, "_e", None) and self._e.value:
+            self.lib.flic_ensemble_destroy(self._e)
+            self._e = ctypes.c_void_p()
 
     def __enter__(self):
         return self
