@@ -41,7 +41,10 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--config", default="head-on-256",
+                   choices=("head-on-256", "ensemble-64", "off-axis-512", "disc-128", "sphere-32"),
+                   help="workload; the default is the headline 256^3 head-on collision")
+    p.add_argument("--n", type=int, default=256, help="grid size of the head-on collision")
     p.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--fp64-steps", type=int, default=10)
@@ -229,29 +232,54 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def main(argv=None):
-    args = parse_args(argv)
-    if args.impl == "reference":
-        return reference_arm(args)
-    rank, world, local = dist_env()
+def make_workload(args, rank):
+    """(setup, poisson, name) of a single-grid configuration."""
+    from paper_1311_0861_gb300 import inputs
+    if args.config == "head-on-256":
+        n = args.n
+        setup = inputs.head_on(n) if rank == 0 else inputs.collision(n, seed=3 + 1000 * rank)
+        return setup, "periodic", f"head-on two-galaxy collision {n}^3 (seeded synthetic)"
+    if args.config == "off-axis-512":
+        return inputs.off_axis(512), "isolated", "off-axis two-galaxy collision 512^3, isolated gravity"
+    if args.config == "disc-128":
+        return inputs.disc(128), "periodic", "rotating disc galaxy 128^3"
+    if args.config == "sphere-32":
+        return inputs.sphere(32), "periodic", "self-gravitating sphere 32^3"
+    raise ValueError(args.config)
+
+
+def roofline_entry(kern, stage_ms, steps, cells, esz, precision, N):
+    avg_s = stage_ms[kern] / steps / 1e3
+    alg_bytes = ALG_WORDS[kern] * esz * cells
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / avg_s / 1e9
+    r = {"bound": "hbm", "kernel": f"fluid_step_kernel<{'Bme' if kern == 'bme' else 'Gas'}Phys>",
+         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+         "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3}
+    # ncu DRAM bytes per launch, recorded for a given kernel source: used only
+    # while the kernel source is unchanged
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file) and N is not None:
+        try:
+            import hashlib
+            rec = json.load(open(traffic_file))
+            src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == rec["sha256_16"]:
+                r["traffic"] = rec.get(f"{kern}-{precision}-{N}")
+        except Exception:
+            pass
+    return r
+
+
+def run_single(args, rank, world, stream, clocks):
     import torch
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-    torch.cuda.set_device(local)
     from paper_1311_0861_gb300 import flic, inputs
-    if not os.path.exists(flic.LIB_PATH):
-        from paper_1311_0861_gb300 import build
-        build.build()
-    N = args.n
-    setup = inputs.head_on(N) if rank == 0 else inputs.collision(N, seed=3 + 1000 * rank)
-    stream = torch.cuda.Stream()
+    setup, poisson, name = make_workload(args, rank)
+    N = setup.shape[0]
     esz = 4 if args.precision == "mixed" else 8
-    g = flic.Grid(N, precision=args.precision, gamma=setup.gamma, stream=stream.cuda_stream)
+    g = flic.Grid(N, precision=args.precision, gamma=setup.gamma, poisson=poisson, stream=stream.cuda_stream)
     g.set_state(setup.state)
     launches = g.launches_per_step()
-
-    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.2)
     clocks.mark("w0")
@@ -262,7 +290,7 @@ def main(argv=None):
     clocks.mark("t0")
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    stage_ms, total_ms = g.profile(args.steps)
+    stage_ms, _ = g.profile(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks.mark("t1")
@@ -272,29 +300,8 @@ def main(argv=None):
     agg = aggregate({"seconds": elapsed_ms / 1e3, "cells": N ** 3 * args.steps}, world)
     value = agg["cells"] / agg["max_s"]
     d = g.step_diagnostics()
-
-    # roofline of the dominant kernel
     kern = max(("gas", "bme"), key=lambda k: stage_ms[k])
-    avg_s = stage_ms[kern] / args.steps / 1e3
-    alg_bytes = ALG_WORDS[kern] * esz * N ** 3
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / avg_s / 1e9
-    roofline = {"bound": "hbm", "kernel": f"fluid_step_kernel<{'Bme' if kern == 'bme' else 'Gas'}Phys>",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind,
-                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3}
-    # ncu DRAM bytes per launch, recorded for a given kernel source: used only
-    # while the kernel source is unchanged
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file):
-        try:
-            import hashlib
-            rec = json.load(open(traffic_file))
-            src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest()[:16] == rec["sha256_16"]:
-                roofline["traffic"] = rec.get(f"{kern}-{args.precision}-{N}")
-        except Exception:
-            pass
+    roofline = roofline_entry(kern, stage_ms, args.steps, N ** 3, esz, args.precision, N)
 
     # ---- end to end through the public API with pinned host buffers ----
     e2e = None
@@ -327,7 +334,7 @@ def main(argv=None):
         g.run(10, sync=True)
         mixed10 = g.get_state()
         g.close()
-        g64 = flic.Grid(N, precision="fp64", gamma=setup.gamma, stream=stream.cuda_stream)
+        g64 = flic.Grid(N, precision="fp64", gamma=setup.gamma, poisson=poisson, stream=stream.cuda_stream)
         g64.set_state(setup.state)
         g64.run(2, sync=True)
         st64, tot64 = g64.profile(args.fp64_steps)
@@ -345,27 +352,126 @@ def main(argv=None):
         g.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and poisson == "periodic":
         r = oracle_sample(setup, 20.0)
         cpu = {"value": r["value"], "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                "sample": (f"numpy FP64 oracle: whole-grid Poisson solve ({r['t_poisson']:.1f} s) + update of "
                           f"{r['planes']} of {N} z-planes ({r['t_slab']:.1f} s), scaled to one full step")}
+    line = {"value": value, "ms_per_step": agg["max_s"] * 1e3 / args.steps,
+            "config": {"workload": name, "n": N, "precision": args.precision,
+                       "poisson": f"{poisson} FFT",
+                       "l2": f"inputs larger than L2 (state {22 * esz * N ** 3 / 2 ** 30:.2f} GiB)"
+                       if 22 * esz * N ** 3 > 2 ** 27 else "state smaller than L2; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches * args.steps,
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "compare": compare, "status": "ok" if not d["nonphysical"] else "nonphysical"}
+    return line
 
+
+def run_ensemble(args, rank, world, stream, clocks):
+    """64 independent collisions of uneven sizes advanced by one batched launch per stage."""
+    import torch
+    from paper_1311_0861_gb300 import flic, inputs
+    members = [inputs.ensemble_member(r) for r in range(64)]
+    sizes = [m.shape[0] for m in members]
+    cells = sum(n ** 3 for n in sizes)
+    esz = 4 if args.precision == "mixed" else 8
+    ens = flic.Ensemble(sizes, precision=args.precision, stream=stream.cuda_stream)
+    for r, m in enumerate(members):
+        ens.set_state(r, m.state)
+    launches = ens.launches_per_step()
+    clocks.start()
+    time.sleep(0.2)
+    clocks.mark("w0")
+    ens.step(args.warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark("t0")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stage_ms, _ = ens.profile(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    barrier(world)
+    clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    agg = aggregate({"seconds": elapsed_ms / 1e3, "cells": cells * args.steps}, world)
+    value = agg["cells"] / agg["max_s"]
+    bad = any(ens.diagnostics(r)["nonphysical"] for r in range(len(sizes)))
+    kern = max(("gas", "bme"), key=lambda k: stage_ms[k])
+    roofline = roofline_entry(kern, stage_ms, args.steps, cells, esz, args.precision, None)
+    # the same runs one after another, each a single-grid handle
+    seq_ms, seq_steps = 0.0, max(1, min(args.steps, 10))
+    for m in members:
+        with flic.Grid(m.shape[0], precision=args.precision, gamma=m.gamma, stream=stream.cuda_stream) as g:
+            g.set_state(m.state)
+            g.run(2, sync=True)
+            _, tot = g.profile(seq_steps)
+            seq_ms += tot
+    seq_value = cells * seq_steps / (seq_ms / 1e3)
+    # end to end: every run's state from host, one step, every state back
+    e2e = None
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for r, m in enumerate(members):
+                ens.set_state(r, m.state)
+            ens.step(1, sync=False)
+            for r in range(len(sizes)):
+                ens.get_state(r)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t
+        e2e = {"value": cells * args.e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 22 * 8 * cells, "d2h_bytes_per_step": 22 * 8 * cells,
+               "steps": args.e2e_steps, "what": "per step: every run's state from host, one step, every state back"}
+    ens.close()
+    counts = {n: sizes.count(n) for n in sorted(set(sizes))}
+    return {"value": value, "ms_per_step": agg["max_s"] * 1e3 / args.steps,
+            "config": {"workload": "64-run collision ensemble, uneven grids " +
+                       ", ".join(f"{c}x{n}^3" for n, c in counts.items()),
+                       "cells_per_step": cells, "precision": args.precision, "poisson": "periodic FFT",
+                       "l2": f"state {22 * esz * cells / 2 ** 30:.2f} GiB",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
+            "gpu_launches": launches * args.steps,
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "compare": {"sequential_value": seq_value, "batched_over_sequential": value / seq_value},
+            "status": "ok" if not bad else "nonphysical"}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_1311_0861_gb300 import flic
+    if not os.path.exists(flic.LIB_PATH):
+        from paper_1311_0861_gb300 import build
+        build.build()
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if args.config == "ensemble-64":
+        res = run_ensemble(args, rank, world, stream, clocks)
+    else:
+        res = run_single(args, rank, world, stream, clocks)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": agg["max_s"] * 1e3 / args.steps,
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-                "config": {"workload": f"head-on two-galaxy collision {N}^3 (seeded synthetic)",
-                           "n": N, "precision": args.precision, "poisson": "periodic FFT",
-                           "l2": f"inputs larger than L2 (state {22 * esz * N ** 3 / 2 ** 30:.2f} GiB)",
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches * args.steps,
-                "clocks": clocks.summary(),
-                "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
-                "compare": compare,
-                "status": "ok" if not d["nonphysical"] else "nonphysical"}
+                "config": res["config"], "roofline": res["roofline"], "cpu_baseline": res["cpu_baseline"],
+                "e2e": res["e2e"], "gpu_launches": res["gpu_launches"], "clocks": clocks.summary(),
+                "stages_ms_per_step": res["stages_ms_per_step"], "compare": res["compare"],
+                "status": res["status"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

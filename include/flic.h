@@ -197,8 +197,11 @@ int flic_ensemble_get_state(flic_ensemble* e, int run, double* const fields[FLIC
 int flic_ensemble_step(flic_ensemble* e, int nsteps, double dt, int sync);
 /* Last step record of one run (same fields as flic_step_diagnostics). */
 int flic_ensemble_diagnostics(flic_ensemble* e, int run, flic_diag* out);
-/* nsteps steps timed with CUDA events on the ensemble's stream. */
-int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double* total_ms);
+/* nsteps steps as plain launches with CUDA events on the ensemble's stream
+ * between stages (the stages of flic_profile); stage_ms[k] summed over steps,
+ * *total_ms (nullable) first to last event. */
+int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double stage_ms[FLIC_NSTAGES],
+                          double* total_ms);
 int flic_ensemble_launches_per_step(flic_ensemble* e);
 int flic_ensemble_destroy(flic_ensemble* e);
 const char* flic_ensemble_last_error(flic_ensemble* e);

@@ -82,7 +82,8 @@ struct flic_ensemble {
 namespace {
 
 template <typename T>
-int ens_enqueue_step(flic_ensemble* e, double dt) {
+int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
+    if (ev) ENS_CK(e, cudaEventRecord(ev[0], e->st));
     ENS_CK(e, step_prep_batch(e->prep_tab, e->nruns, dt, e->st));
     if (e->d.G != 0.0) {
         for (auto& c : e->classes) {
@@ -99,16 +100,22 @@ int ens_enqueue_step(flic_ensemble* e, double dt) {
             }
         }
     }
+    if (ev) ENS_CK(e, cudaEventRecord(ev[1], e->st));
     ENS_CK(e, launch_gas_batch<T>(reinterpret_cast<const StencilArgs<T>*>(e->tab_gas[e->cur]), e->work_gas,
                                   e->nwork_gas, e->st));
+    if (ev) ENS_CK(e, cudaEventRecord(ev[2], e->st));
     ENS_CK(e, launch_bme_batch<T>(reinterpret_cast<const StencilArgs<T>*>(e->tab_bme[e->cur]), e->work_bme,
                                   e->nwork_bme, e->st));
+    if (ev) ENS_CK(e, cudaEventRecord(ev[3], e->st));
     ENS_CK(e, step_finalize_batch(e->fin_tab, e->nruns, 1, e->st));
+    if (ev) ENS_CK(e, cudaEventRecord(ev[4], e->st));
     e->cur = 1 - e->cur;
     return FLIC_OK;
 }
 
-int ens_step(flic_ensemble* e, double dt) { return e->fp64 ? ens_enqueue_step<double>(e, dt) : ens_enqueue_step<float>(e, dt); }
+int ens_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
+    return e->fp64 ? ens_enqueue_step<double>(e, dt, ev) : ens_enqueue_step<float>(e, dt, ev);
+}
 
 void ens_free(flic_ensemble* e) {
     for (int i = 0; i < 2; ++i) {
@@ -448,22 +455,36 @@ int flic_ensemble_diagnostics(flic_ensemble* e, int run, flic_diag* out) {
     return FLIC_OK;
 }
 
-int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double* total_ms) {
-    if (!e || nsteps <= 0 || !total_ms) return FLIC_ERR_INVALID_ARG;
-    cudaEvent_t a, b;
-    ENS_CK(e, cudaEventCreate(&a));
-    ENS_CK(e, cudaEventCreate(&b));
-    ENS_CK(e, cudaEventRecord(a, e->st));
-    int rc = flic_ensemble_step(e, nsteps, dt, 0);
-    if (rc == FLIC_OK) {
-        ENS_CK(e, cudaEventRecord(b, e->st));
-        ENS_CK(e, cudaEventSynchronize(b));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        *total_ms = ms;
+int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double stage_ms[FLIC_NSTAGES],
+                          double* total_ms) {
+    if (!e || nsteps <= 0 || !stage_ms) return FLIC_ERR_INVALID_ARG;
+    const int ne = 5 * nsteps;
+    std::vector<cudaEvent_t> ev(ne);
+    int made = 0, rc = FLIC_OK;
+    for (; made < ne; ++made) {
+        cudaError_t er = cudaEventCreate(&ev[made]);
+        if (er != cudaSuccess) { e->err = cudaGetErrorString(er); rc = FLIC_ERR_CUDA; break; }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    for (int s = 0; rc == FLIC_OK && s < nsteps; ++s) rc = ens_step(e, dt, ev.data() + 5 * s);
+    if (rc == FLIC_OK) {
+        cudaError_t er = cudaEventSynchronize(ev[ne - 1]);
+        if (er != cudaSuccess) { e->err = cudaGetErrorString(er); rc = FLIC_ERR_CUDA; }
+    }
+    if (rc == FLIC_OK) {
+        for (int k = 0; k < FLIC_NSTAGES; ++k) stage_ms[k] = 0.0;
+        for (int s = 0; s < nsteps; ++s)
+            for (int k = 0; k < FLIC_NSTAGES; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[5 * s + k], ev[5 * s + k + 1]);
+                stage_ms[k] += ms;
+            }
+        if (total_ms) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[ne - 1]);
+            *total_ms = ms;
+        }
+    }
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
 

@@ -93,7 +93,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.flic_ensemble_get_state.argtypes = [P, ctypes.c_int, ctypes.POINTER(P)]
     lib.flic_ensemble_step.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int]
     lib.flic_ensemble_diagnostics.argtypes = [P, ctypes.c_int, ctypes.POINTER(Diag)]
-    lib.flic_ensemble_profile.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.flic_ensemble_profile.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
     lib.flic_ensemble_launches_per_step.argtypes = [P]
     lib.flic_ensemble_destroy.argtypes = [P]
     lib.flic_ensemble_last_error.argtypes = [P]
@@ -336,10 +337,13 @@ class Ensemble:
         self._check(self.lib.flic_ensemble_diagnostics(self._e, run, ctypes.byref(d)))
         return d.as_dict()
 
-    def profile(self, nsteps: int, dt: float = 0.0) -> float:
-        ms = ctypes.c_double()
-        self._check(self.lib.flic_ensemble_profile(self._e, int(nsteps), dt, ctypes.byref(ms)))
-        return ms.value
+    def profile(self, nsteps: int, dt: float = 0.0):
+        """Per-stage device milliseconds summed over ``nsteps`` plain-launch steps,
+        and the total elapsed milliseconds."""
+        ms = (ctypes.c_double * NSTAGES)()
+        tot = ctypes.c_double()
+        self._check(self.lib.flic_ensemble_profile(self._e, int(nsteps), dt, ms, ctypes.byref(tot)))
+        return dict(zip(STAGES, list(ms))), tot.value
 
     def launches_per_step(self) -> int:
         return self._check(self.lib.flic_ensemble_launches_per_step(self._e))
