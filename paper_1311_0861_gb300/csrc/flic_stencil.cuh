@@ -13,14 +13,15 @@
 //     diagonal is positive, else reset nE = Pi + q q^T/n.
 //
 // Structure (2.5D z-march).  A block owns a TX x TY column tile and a chunk of
-// z planes.  It walks up the chunk with a two-plane ring of the input state in
-// shared memory over the tile plus a 2-cell halo (R2).  Per plane e:
+// z planes.  It walks up the chunk with a ring of input planes in shared memory
+// over the tile plus a 2-cell halo (R2).  Per plane e (two barriers):
 //   S0  asynchronous 8-byte copies of plane e+2 into a three-slot ring (the
 //       fields the faces need, + Phi), one full iteration ahead of its use;
-//   S1  x- and y-face solutions of plane e over the tile plus a 1-cell halo (R1);
 //   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
 //   S3  upwind fluxes of f' for the tile cells; plane e-1 completes (its +z flux
-//       needs f'_e), gets the energy balance and is written out.
+//       needs f'_e), gets the energy balance and is written out;
+//   S1  (same phase as S3) x- and y-face solutions of plane e+1 over the tile
+//       plus a 1-cell halo (R1), for the next S2.
 // The transported state f' of the tile cell, its partial sum and the last z-flux
 // live in registers of the thread that owns the column.
 #pragma once
@@ -494,45 +495,54 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     T vmax = T(0);
     bool bad = false;
 
+    // x / y face solutions of plane pe over the tile + 1-cell halo (S1)
+    auto xy_faces = [&](const T* rpe) {
+        for (int i = tid; i < NXF + NYF; i += NT) {
+            T v[NFACE];
+            if (i < NXF) {
+                const int fx = i % Gm::XFW, jy = i / Gm::XFW;
+                const int a2 = (jy + 1) * W2 + fx;
+                P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
+            } else {
+                const int j = i - NXF;
+                const int jx = j % W1, fy = j / W1;
+                const int a2 = fy * W2 + jx + 1;
+                P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) yf[k * NYF + j] = v[k];
+            }
+        }
+    };
+
+    // Two barriers per plane.  Iteration e:
+    //   [copies of planes e, e+1 landed; barrier]
+    //   phase 1: z faces e+1/2 and the Eulerian update of plane e over R1 (S2)
+    //   [barrier]
+    //   phase 2: Lagrangian fluxes of the own cell at plane e (S3), then the x/y
+    //            faces of plane e+1 (S1) -- the own cell's face velocities were
+    //            kept in registers in phase 1, so the face buffers can be reused
     issue_plane(z0 - 2);
-    for (int p = z0 - 2; p <= z1 + 1; ++p) {
-        const T* rp = ring + ring_slot(p) * NR * R2;       // plane p
-        const T* re = ring + ring_slot(p - 1) * NR * R2;   // plane e = p - 1
-        const int e = p - 1;
-        const bool active = (p >= z0);
-        // plane p + 1 goes into the slot of plane p - 2 (last read by S2 of the
-        // previous iteration, before its closing barrier)
-        if (p + 1 <= z1 + 1) {
-            // the extra fields of plane p are read by S2 of the next iteration
-            if (SEX && NEX > 0 && p >= z0 - 1) issue_extra(p);
-            issue_plane(p + 1);
+    issue_plane(z0 - 1);
+    T Wxm = T(0), Wxp = T(0), Wym = T(0), Wyp = T(0);
+    for (int e = z0 - 2; e <= z1; ++e) {
+        const T* re = ring + ring_slot(e) * NR * R2;       // plane e
+        const T* rp = ring + ring_slot(e + 1) * NR * R2;   // plane e + 1
+        // plane e + 2 goes into the slot of plane e - 1 (last read in phase 1
+        // of the previous iteration); the staged extra fields of plane e + 1
+        // (read in phase 1 of the next iteration) travel in the same group
+        if (e + 2 <= z1 + 1) {
+            if (SEX && NEX > 0 && e + 1 >= z0 - 1) issue_extra(e + 1);
+            issue_plane(e + 2);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
-        // ---- S1: x/y faces of plane e ---------------------------------------
-        if (active) {
-            for (int i = tid; i < NXF; i += NT) {
-                const int fx = i % Gm::XFW, jy = i / Gm::XFW;
-                const int a2 = (jy + 1) * W2 + fx;
-                T v[NFACE];
-                P::face(re, a2, re, a2 + 1, R2, 0, gamma, v);
-#pragma unroll
-                for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
-            }
-            for (int i = tid; i < NYF; i += NT) {
-                const int jx = i % W1, fy = i / W1;
-                const int a2 = fy * W2 + jx + 1;
-                T v[NFACE];
-                P::face(re, a2, re, a2 + W2, R2, 1, gamma, v);
-#pragma unroll
-                for (int k = 0; k < NFACE; ++k) yf[k * NYF + i] = v[k];
-            }
-        }
-        __syncthreads();
-        // ---- S2: z face e+1/2 and Eulerian update of plane e over R1 ---------
-        if (p >= z0 - 1) {
+        const bool active = (e >= z0 - 1);   // f' of plane e is needed
+        // ---- phase 1: z face e+1/2 and Eulerian update of plane e over R1 ----
+        {
             const size_t zoff_e = size_t(e < 0 ? e + N : (e >= N ? e - N : e)) * plane;
             for (int i = tid; i < R1; i += NT) {
                 int jx, jy;
@@ -573,8 +583,13 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
 #pragma unroll
                     for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
                     if (i == tid) {
-                        // own tile cell: keep the -z face velocity for S3
+                        // own tile cell: keep its face normal velocities for phase 2
+                        // (gas: V first on every axis; moments: u*_d is value d)
                         wz_prev = P::normal_velocity(fm[2], 2);
+                        Wxm = P::normal_velocity(fm[0], 0);
+                        Wxp = P::normal_velocity(fpv[0], 0);
+                        Wym = P::normal_velocity(fm[1], 1);
+                        Wyp = P::normal_velocity(fpv[1], 1);
                         if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
                     }
                 }
@@ -584,17 +599,8 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             }
         }
         __syncthreads();
-        if (!active) continue;
-        // ---- S3: Lagrangian fluxes of the own tile cell --------------------
-        {
-            const int cx = own_tx + 1, cy = own_ty + 1;
-            // face normal velocities W (gas: V stored first on every axis;
-            // moments: u*_d is value d of an axis-d face)
-            constexpr int KY = (NFACE == 2) ? 0 : 1;
-            const T Wxm = xf[cy * Gm::XFW + cx];
-            const T Wxp = xf[cy * Gm::XFW + cx + 1];
-            const T Wym = yf[KY * NYF + cy * W1 + cx];
-            const T Wyp = yf[KY * NYF + (cy + 1) * W1 + cx];
+        // ---- phase 2: Lagrangian fluxes of the own tile cell (plane e) -----
+        if (active) {
             const T Wzm = wz_prev;
             T out[NF];
 #pragma unroll
@@ -619,6 +625,8 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 for (int f = 0; f < NF; ++f) a.out[f * a.fs + g] = out[f];
             }
         }
+        // ---- phase 2: x/y faces of plane e + 1 ----------------------------
+        if (e + 1 <= z1) xy_faces(rp);
     }
     cp_async_wait<0>();
 
