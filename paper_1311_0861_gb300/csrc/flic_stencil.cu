@@ -6,36 +6,38 @@ namespace flic {
 namespace {
 
 template <typename T> struct Tiles;
-// Column tiles, minimum resident blocks per SM (register budget) and whether
-// the moment energy tensor is staged in shared memory (BS) or read directly.
-// float32 moments: 32 x 8 tiles, two blocks per SM (measured faster than one
-// 32 x 16 block with staging, whose single 16-warp barrier group issues worse).
+// Launch shapes (TileCfg: tile, min blocks per SM, staged energy tensor, one
+// thread per updated cell, helper face rounds), chosen by measurement at 256^3.
+// float32 gas: 32 x 8, one thread per tile cell, three blocks per SM.
+// float32 moments: 32 x 12 with 480 threads (384 tile + 96 helpers), one block
+// per SM and no register cap -- faster than 256-thread blocks two per SM, whose
+// 128-register cap spills and whose border cells take a second phase-1 round.
 template <> struct Tiles<float> {
-    static constexpr int GX = 32, GY = 8, GB = 3, BX = 32, BY = 8, BB = 2;
-    static constexpr bool BS = false;
+    using Gas = TileCfg<32, 8, 3, false, false, 0>;
+    using Bme = TileCfg<32, 12, 1, false, true, 6>;
 };
 template <> struct Tiles<double> {
-    static constexpr int GX = 32, GY = 8, GB = 2, BX = 32, BY = 4, BB = 1;
-    static constexpr bool BS = true;
+    using Gas = TileCfg<32, 8, 2, false, false, 0>;
+    using Bme = TileCfg<32, 4, 1, true, true, 4>;
 };
 
 // Launch geometry: the z-chunk height minimises (waves of resident blocks) x
 // (planes a block marches, including its 4-plane warm-up), using the kernel's
 // measured occupancy and the device's SM count.
-template <class P, typename T, int TX, int TY, int MB, bool SX>
+template <class P, typename T, class C>
 StepCfg make_cfg(int N, int tz) {
     StepCfg c;
-    c.tx = TX;
-    c.ty = TY;
-    c.tiles_x = (N + TX - 1) / TX;
-    c.tiles_y = (N + TY - 1) / TY;
-    c.threads = TX * TY;
-    c.smem = Geom<P, T, TX, TY, SX>::smem_bytes;
+    c.tx = C::TX;
+    c.ty = C::TY;
+    c.tiles_x = (N + C::TX - 1) / C::TX;
+    c.tiles_y = (N + C::TY - 1) / C::TY;
+    c.threads = Geom<P, T, C>::NTH;
+    c.smem = Geom<P, T, C>::smem_bytes;
     if (tz <= 0) {
         int dev = 0, sms = 152, per_sm = 1;
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_step_kernel<P, T, TX, TY, MB, SX>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_step_kernel<P, T, C>,
                                                       c.threads, c.smem);
         if (per_sm < 1) per_sm = 1;
         const long slots = long(sms) * per_sm;
@@ -55,52 +57,52 @@ StepCfg make_cfg(int N, int tz) {
     return c;
 }
 
-template <class P, typename T, int TX, int TY, int MB, bool SX>
+template <class P, typename T, class C>
 cudaError_t prepare() {
-    return cudaFuncSetAttribute(fluid_step_kernel<P, T, TX, TY, MB, SX>,
+    return cudaFuncSetAttribute(fluid_step_kernel<P, T, C>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Geom<P, T, TX, TY, SX>::smem_bytes);
+                                (int)Geom<P, T, C>::smem_bytes);
 }
 
-template <class P, typename T, int TX, int TY, int MB, bool SX>
+template <class P, typename T, class C>
 cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
     BatchArgs<T> none{nullptr, nullptr};
-    fluid_step_kernel<P, T, TX, TY, MB, SX>
+    fluid_step_kernel<P, T, C>
         <<<dim3(c.tiles_x * c.tiles_y, c.blocks_z), c.threads, c.smem, st>>>(a, none);
     return cudaGetLastError();
 }
 
-template <class P, typename T, int TX, int TY, int MB, bool SX>
+template <class P, typename T, class C>
 cudaError_t launch_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
     StencilArgs<T> unused{};
     BatchArgs<T> b{table, work};
-    fluid_step_kernel<P, T, TX, TY, MB, SX>
-        <<<nwork, TX * TY, Geom<P, T, TX, TY, SX>::smem_bytes, st>>>(unused, b);
+    fluid_step_kernel<P, T, C>
+        <<<nwork, Geom<P, T, C>::NTH, Geom<P, T, C>::smem_bytes, st>>>(unused, b);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 template <typename T> StepCfg gas_cfg(int N, int tz) {
-    return make_cfg<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB, false>(N, tz);
+    return make_cfg<GasPhys<T>, T, typename Tiles<T>::Gas>(N, tz);
 }
 template <typename T> StepCfg bme_cfg(int N, int tz) {
-    return make_cfg<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB, Tiles<T>::BS>(N, tz);
+    return make_cfg<BmePhys<T>, T, typename Tiles<T>::Bme>(N, tz);
 }
 template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-    return launch<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB, false>(a, c, st);
+    return launch<GasPhys<T>, T, typename Tiles<T>::Gas>(a, c, st);
 }
 template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-    return launch<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB, Tiles<T>::BS>(a, c, st);
+    return launch<BmePhys<T>, T, typename Tiles<T>::Bme>(a, c, st);
 }
 
 template <typename T>
 cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
-    return launch_batch<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB, false>(table, work, nwork, st);
+    return launch_batch<GasPhys<T>, T, typename Tiles<T>::Gas>(table, work, nwork, st);
 }
 template <typename T>
 cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
-    return launch_batch<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB, Tiles<T>::BS>(table, work, nwork,
+    return launch_batch<BmePhys<T>, T, typename Tiles<T>::Bme>(table, work, nwork,
                                                                                               st);
 }
 template cudaError_t launch_gas_batch<float>(const StencilArgs<float>*, const WorkItem*, int, cudaStream_t);
@@ -109,9 +111,9 @@ template cudaError_t launch_bme_batch<float>(const StencilArgs<float>*, const Wo
 template cudaError_t launch_bme_batch<double>(const StencilArgs<double>*, const WorkItem*, int, cudaStream_t);
 
 template <typename T> cudaError_t stencil_prepare() {
-    cudaError_t e = prepare<GasPhys<T>, T, Tiles<T>::GX, Tiles<T>::GY, Tiles<T>::GB, false>();
+    cudaError_t e = prepare<GasPhys<T>, T, typename Tiles<T>::Gas>();
     if (e != cudaSuccess) return e;
-    return prepare<BmePhys<T>, T, Tiles<T>::BX, Tiles<T>::BY, Tiles<T>::BB, Tiles<T>::BS>();
+    return prepare<BmePhys<T>, T, typename Tiles<T>::Bme>();
 }
 template cudaError_t stencil_prepare<float>();
 template cudaError_t stencil_prepare<double>();

@@ -14,14 +14,18 @@
 //
 // Structure (2.5D z-march).  A block owns a TX x TY column tile and a chunk of
 // z planes.  It walks up the chunk with a ring of input planes in shared memory
-// over the tile plus a 2-cell halo (R2).  Per plane e (two barriers):
+// over the tile plus a 2-cell halo (R2).  Thread i < TX*TY owns tile column i;
+// the block has one thread per cell of the tile and its four 1-cell edge
+// strips (rounded up to whole warps), so the Eulerian update of a plane is one
+// item per thread.  Per plane e (two barriers):
 //   S0  asynchronous 8-byte copies of plane e+2 into a three-slot ring (the
 //       fields the faces need, + Phi), one full iteration ahead of its use;
 //   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
 //   S3  upwind fluxes of f' for the tile cells; plane e-1 completes (its +z flux
 //       needs f'_e), gets the energy balance and is written out;
 //   S1  (same phase as S3) x- and y-face solutions of plane e+1 over the tile
-//       plus a 1-cell halo (R1), for the next S2.
+//       plus a 1-cell halo (R1), for the next S2; the threads without a tile
+//       column start on them while the others run S3.
 // The transported state f' of the tile cell, its partial sum and the last z-flux
 // live in registers of the thread that owns the column.
 #pragma once
@@ -330,11 +334,32 @@ struct BmePhys {
 // ---------------------------------------------------------------------------
 constexpr int RING_SLOTS = 3;   // planes e, e+1 in use, e+2 in flight
 
-template <class P, typename T, int TX, int TY, bool SEX>
+// Launch shape of a fluid kernel: TX x TY column tile, minimum resident blocks
+// per SM (register budget), whether the moment energy tensor is staged in
+// shared memory (SEX), whether the block has one thread per updated cell (WIDE;
+// else one per tile cell, looping over the border cells) and how many x/y faces
+// each thread without a tile cell takes first (HR).
+template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_>
+struct TileCfg {
+    static constexpr int TX = TX_, TY = TY_, MINB = MINB_, HR = HR_;
+    static constexpr bool SEX = SEX_, WIDE = WIDE_;
+};
+
+template <class P, typename T, class C>
 struct Geom {
-    static constexpr int NT = TX * TY;
+    static constexpr int TX = C::TX, TY = C::TY;
+    static constexpr bool SEX = C::SEX;
+    static constexpr int NT = TX * TY;                               // tile (own) cells
     static constexpr int W2 = TX + 4, H2 = TY + 4, R2 = W2 * H2;   // tile + 2 halo
     static constexpr int W1 = TX + 2, H1 = TY + 2, R1 = W1 * H1;   // tile + 1 halo
+    // cells updated by the Eulerian stage: the tile and its four edge strips
+    // (the corners of the 1-cell border feed no tile cell's flux)
+    static constexpr int NU = NT + 2 * TX + 2 * TY;
+    // threads: WIDE -- one updated cell each in phase 1, and the NTH - NT
+    // threads without a tile cell (helpers) take x/y faces while the tile
+    // threads run S3; else one per tile cell
+    static constexpr int NTH = C::WIDE ? (NU + 31) / 32 * 32 : NT;
+    static_assert(NTH <= 1024, "tile too large for one block");
     static constexpr int XFW = TX + 3;                               // x faces per R1 row
     static constexpr int YFH = TY + 3;                               // y-face rows
     static constexpr int CH = 8 / sizeof(T);                         // elements per 8-byte copy
@@ -359,8 +384,8 @@ struct Geom {
     static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (CPR + H2);
 };
 
-// R1 cell i -> (jx, jy), tile cells first (so that i == threadIdx.x is the
-// thread's own column), then the one-cell border.
+// Updated cell i -> R1 coordinates (jx, jy): tile cells first (so that thread i
+// owns the column of tile cell i), then the four edge strips of the border.
 template <int TX, int TY>
 __device__ __forceinline__ void r1_coords(int i, int& jx, int& jy) {
     if (i < TX * TY) {
@@ -369,10 +394,10 @@ __device__ __forceinline__ void r1_coords(int i, int& jx, int& jy) {
         return;
     }
     int h = i - TX * TY;
-    if (h < TX + 2) { jx = h; jy = 0; return; }
-    h -= TX + 2;
-    if (h < TX + 2) { jx = h; jy = TY + 1; return; }
-    h -= TX + 2;
+    if (h < TX) { jx = 1 + h; jy = 0; return; }
+    h -= TX;
+    if (h < TX) { jx = 1 + h; jy = TY + 1; return; }
+    h -= TX;
     if (h < TY) { jx = 0; jy = 1 + h; return; }
     h -= TY;
     jx = TX + 1;
@@ -391,11 +416,14 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 __device__ __forceinline__ int ring_slot(int p) { return ((p % RING_SLOTS) + RING_SLOTS) % RING_SLOTS; }
 
-template <class P, typename T, int TX, int TY, int MINB, bool SEX>
-__global__ void __launch_bounds__(TX * TY, MINB)
+template <class P, typename T, class C>
+__global__ void __launch_bounds__(Geom<P, T, C>::NTH, C::MINB)
 fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
-    using Gm = Geom<P, T, TX, TY, SEX>;
+    using Gm = Geom<P, T, C>;
+    constexpr int TX = C::TX, TY = C::TY;
+    constexpr bool SEX = C::SEX;
     constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, H2 = Gm::H2, R1 = Gm::R1, W1 = Gm::W1;
+    constexpr int NTH = Gm::NTH, NU = Gm::NU;
     constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE, NEX = P::NEX;
     constexpr int NXF = Gm::H1 * Gm::XFW;
     constexpr int NYF = Gm::YFH * W1;
@@ -439,13 +467,14 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     const T gamma = a.gamma, eta = a.eta;
 
     // x0 - 2 and N are multiples of CH, so no chunk straddles the periodic wrap
-    for (int i = tid; i < CPR; i += NT) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
-    for (int i = tid; i < H2; i += NT) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
+    for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
+    for (int i = tid; i < H2; i += NTH) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
     __syncthreads();
 
-    // own tile cell
-    const int own_tx = tid % TX, own_ty = tid / TX;
-    const bool own_valid = (x0 + own_tx < N) && (y0 + own_ty < N);
+    // own tile cell (threads tid < NT)
+    const bool own_tile = tid < NT;
+    const int own_tx = own_tile ? tid % TX : 0, own_ty = own_tile ? tid / TX : 0;
+    const bool own_valid = own_tile && (x0 + own_tx < N) && (y0 + own_ty < N);
     const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
 
     // S0 of plane pz: asynchronous 8-byte copies of the ring fields of the plane
@@ -456,7 +485,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         T* dst = ring + ring_slot(pz) * NR * R2;
         const int zw = pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
         const size_t zoff = size_t(zw) * plane;
-        for (int pos = tid; pos < NPOS; pos += NT) {
+        for (int pos = tid; pos < NPOS; pos += NTH) {
             const int iy = pos / CPR, c = pos % CPR;
             T* d = dst + iy * W2 + c * CH;
             const size_t goff = zoff + size_t(yoff[iy]) + xoff[c];
@@ -474,7 +503,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         T* dst = exb + (pz & 1) * Gm::ex_slot;
         const int zw = pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
         const size_t zoff = size_t(zw) * plane;
-        for (int pos = tid; pos < NPOS1; pos += NT) {
+        for (int pos = tid; pos < NPOS1; pos += NTH) {
             const int jy = pos / CPR, c = pos % CPR;
             T* d = dst + jy * W2 + c * CH;
             const T* src = a.in + zoff + size_t(yoff[jy + 1]) + xoff[c];
@@ -495,25 +524,34 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     T vmax = T(0);
     bool bad = false;
 
-    // x / y face solutions of plane pe over the tile + 1-cell halo (S1)
-    auto xy_faces = [&](const T* rpe) {
-        for (int i = tid; i < NXF + NYF; i += NT) {
-            T v[NFACE];
-            if (i < NXF) {
-                const int fx = i % Gm::XFW, jy = i / Gm::XFW;
-                const int a2 = (jy + 1) * W2 + fx;
-                P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
+    // x / y face solutions of plane pe over the tile + 1-cell halo (S1).  The
+    // helpers take the first NH * HR faces (they have no S3 work); the rest go
+    // round-robin over all threads.
+    constexpr int NH = NTH - NT;
+    constexpr int HF = (NH * C::HR < NXF + NYF) ? NH * C::HR : NXF + NYF;
+    auto face_item = [&](const T* rpe, int i) {
+        T v[NFACE];
+        if (i < NXF) {
+            const int fx = i % Gm::XFW, jy = i / Gm::XFW;
+            const int a2 = (jy + 1) * W2 + fx;
+            P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
-            } else {
-                const int j = i - NXF;
-                const int jx = j % W1, fy = j / W1;
-                const int a2 = fy * W2 + jx + 1;
-                P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
+            for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
+        } else {
+            const int j = i - NXF;
+            const int jx = j % W1, fy = j / W1;
+            const int a2 = fy * W2 + jx + 1;
+            P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) yf[k * NYF + j] = v[k];
-            }
+            for (int k = 0; k < NFACE; ++k) yf[k * NYF + j] = v[k];
         }
+    };
+    auto xy_faces = [&](const T* rpe) {
+        if constexpr (NH > 0) {
+            if (!own_tile)
+                for (int i = tid - NT; i < HF; i += NH) face_item(rpe, i);
+        }
+        for (int i = HF + tid; i < NXF + NYF; i += NTH) face_item(rpe, i);
     };
 
     // Two barriers per plane.  Iteration e:
@@ -544,7 +582,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         // ---- phase 1: z face e+1/2 and Eulerian update of plane e over R1 ----
         {
             const size_t zoff_e = size_t(e < 0 ? e + N : (e >= N ? e - N : e)) * plane;
-            for (int i = tid; i < R1; i += NT) {
+            for (int i = tid; i < NU; i += NTH) {
                 int jx, jy;
                 r1_coords<TX, TY>(i, jx, jy);
                 const int c1 = jy * W1 + jx;
@@ -582,8 +620,8 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                     P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
 #pragma unroll
                     for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
-                    if (i == tid) {
-                        // own tile cell: keep its face normal velocities for phase 2
+                    if (i < NT) {
+                        // own tile cell (i == tid): keep its face normal velocities for phase 2
                         // (gas: V first on every axis; moments: u*_d is value d)
                         wz_prev = P::normal_velocity(fm[2], 2);
                         Wxm = P::normal_velocity(fm[0], 0);
@@ -600,18 +638,20 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         }
         __syncthreads();
         // ---- phase 2: Lagrangian fluxes of the own tile cell (plane e) -----
-        if (active) {
+        if (active && own_tile) {
             const T Wzm = wz_prev;
+            // upwind cell of each lateral face (the own cell where the face
+            // velocity points away from it)
+            const int cxm = own_c1 - (Wxm > T(0) ? 1 : 0);
+            const int cxp = own_c1 + (Wxp > T(0) ? 0 : 1);
+            const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
+            const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
             T out[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const T* F = fpb + f * R1;
                 const T fc = F[own_c1];
-                T uxm = fc, uxp = fc, uym = fc, uyp = fc;
-                if (Wxm > T(0)) uxm = F[own_c1 - 1];
-                if (!(Wxp > T(0))) uxp = F[own_c1 + 1];
-                if (Wym > T(0)) uym = F[own_c1 - W1];
-                if (!(Wyp > T(0))) uyp = F[own_c1 + W1];
+                const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
                 const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
                 out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
                 acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
@@ -622,7 +662,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 P::finish(out, gamma, eta, q, vmax, bad);
                 const size_t g = size_t(l) * plane + own_g;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) a.out[f * a.fs + g] = out[f];
+                for (int f = 0; f < NF; ++f) __stcs(a.out + f * a.fs + g, out[f]);   // streaming global store
             }
         }
         // ---- phase 2: x/y faces of plane e + 1 ----------------------------
@@ -632,7 +672,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
 
     // ---- block reduction of the conserved sums, kappa and the signal speed ----
     const int lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = NT / 32;
+    constexpr int NW = NTH / 32;
 #pragma unroll
     for (int k = 0; k < P::NQ; ++k) {
         double v = warp_sum(q[k].value());
