@@ -37,21 +37,20 @@ __global__ void green_real_kernel(T* __restrict__ g, int L, T gh2, T self) {
 // z forward transform of the y-transformed Green's function; keeps Re (the
 // transform of an even real function is real) for kz, ky <= L/2, scaled
 template <typename T, int L>
-__global__ void __launch_bounds__(256) fft_z_green(const typename C2<T>::t* __restrict__ spec,
-                                                   const typename C2<T>::t* __restrict__ tw, T scale,
-                                                   T* __restrict__ gtab) {
+__global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_green(const typename C2<T>::t* __restrict__ spec,
+                                                                  const typename C2<T>::t* __restrict__ tw,
+                                                                  T scale, T* __restrict__ gtab) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
-    constexpr int MH = Gm::MH, KB = Gm::KB;
+    constexpr int MH = Gm::MH, KB = Gm::KB, NTC = Gm::NTC;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
-    C* B = A + L * KB;
-    C* tws = B + L * KB;
+    C* tws = A + L * KB;
     stage_twiddles<C, L>(tws, tw);
     const int k0 = blockIdx.x * KB;
     const int y = blockIdx.y;   // 0 .. L/2
     constexpr size_t zs = size_t(L) * MH;
-    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+    for (int t = threadIdx.x; t < L * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
         C v;
         if (k0 + c < MH) v = spec[size_t(y) * MH + size_t(z) * zs + k0 + c];
@@ -59,10 +58,10 @@ __global__ void __launch_bounds__(256) fft_z_green(const typename C2<T>::t* __re
         A[z * KB + c] = v;
     }
     __syncthreads();
-    C* R = Stockham<C, false, L, KB, KB, 1, true, 1, L, L>::run(A, B, tws);
-    for (int t = threadIdx.x; t < (L / 2 + 1) * KB; t += blockDim.x) {
+    StockhamIP<C, false, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
+    for (int t = threadIdx.x; t < (L / 2 + 1) * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
-        if (k0 + c < MH) gtab[(size_t(z) * (L / 2 + 1) + y) * MH + k0 + c] = R[z * KB + c].x * scale;
+        if (k0 + c < MH) gtab[(size_t(z) * (L / 2 + 1) + y) * MH + k0 + c] = A[z * KB + c].x * scale;
     }
 }
 
@@ -96,9 +95,9 @@ static cudaError_t green_init_n(double h, double G, T* gtab, T* greal, void* tmp
     const int gx = (nrows + Gm::RB - 1) / Gm::RB;
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
     fft_x_forward<T, L, L><<<gx, 256, Gm::smem_x, st>>>(greal, nullptr, spec, nrows, tw, 0, 0);
-    fft_y<T, L, L, false><<<dim3(gk, L), 256, Gm::smem_c, st>>>(spec, tw, 0);
+    fft_y<T, L, L, false><<<dim3(gk, L), Gm::NTC, Gm::smem_c, st>>>(spec, tw, 0);
     const double scale = 1.0 / (double(L / 2) * L * L);
-    fft_z_green<T, L><<<dim3(gk, L / 2 + 1), 256, Gm::smem_c, st>>>(spec, tw, T(scale), gtab);
+    fft_z_green<T, L><<<dim3(gk, L / 2 + 1), Gm::NTC, Gm::smem_c, st>>>(spec, tw, T(scale), gtab);
     return cudaGetLastError();
 }
 
@@ -114,9 +113,9 @@ static cudaError_t solve_iso_n(const T* rho, const T* nd, T* phi, void* spec_v, 
     const int gx = (nrows + Gm::RB - 1) / Gm::RB;
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
     fft_x_forward<T, L, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
-    fft_y<T, L, N, false><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, bs_spec);
-    fft_z_solve<T, L, N, true><<<dim3(gk, L, nb), 256, Gm::smem_c, st>>>(spec, tw, nullptr, T(0), gtab, bs_spec);
-    fft_y<T, L, N, true><<<dim3(gk, N, nb), 256, Gm::smem_c, st>>>(spec, tw, bs_spec);
+    fft_y<T, L, N, false><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, bs_spec);
+    fft_z_solve<T, L, N, true><<<dim3(gk, L, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, nullptr, T(0), gtab, bs_spec);
+    fft_y<T, L, N, true><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, bs_spec);
     fft_x_inverse<T, L, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
     return cudaGetLastError();
 }

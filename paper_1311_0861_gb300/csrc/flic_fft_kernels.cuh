@@ -127,17 +127,82 @@ struct Stockham<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL> {
     static __device__ __forceinline__ C* run(C* A, C*, const C*) { return A; }
 };
 
+// In-place Stockham pass for a block of exactly NTHR threads: every thread
+// reads the inputs of its butterflies into registers, the block synchronises,
+// then the outputs overwrite the same buffer (one buffer instead of two, so
+// twice the lines fit in shared memory).
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int R, int TWL, int NTHR>
+__device__ __forceinline__ void stockham_pass_ip(C* A, const C* tw) {
+    constexpr int NB = L / R;
+    constexpr int TOTAL = NB * NL;
+    constexpr int PER = (TOTAL + NTHR - 1) / NTHR;
+    constexpr int TSC = (TWL / L) * (L / (NS * R));
+    C x[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int t = threadIdx.x + p * NTHR;
+        if (TOTAL % NTHR == 0 || t < TOTAL) {
+            const int l = LFAST ? t % NL : t / NB;
+            const int j = LFAST ? t / NL : t % NB;
+#pragma unroll
+            for (int q = 0; q < R; ++q) x[p][q] = A[(j + q * NB) * SJ + l * SL];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int t = threadIdx.x + p * NTHR;
+        if (TOTAL % NTHR == 0 || t < TOTAL) {
+            const int l = LFAST ? t % NL : t / NB;
+            const int j = LFAST ? t / NL : t % NB;
+            const int k = j % NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int q = 1; q < R; ++q) {
+                    C w = tw[q * k * TSC];
+                    if (INV) w.y = -w.y;
+                    x[p][q] = cmul(x[p][q], w);
+                }
+            }
+            Butterfly<C, INV, R>::run(x[p]);
+            const int idx = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) A[(idx + q * NS) * SJ + l * SL] = x[p][q];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int REM, int TWL, int NTHR>
+struct StockhamIP {
+    static __device__ __forceinline__ void run(C* A, const C* tw) {
+        constexpr int R = FirstRadix<REM>::value;
+        static_assert(R > 1, "transform length must be 2^a 3^b");
+        stockham_pass_ip<C, INV, L, NL, SJ, SL, LFAST, NS, R, TWL, NTHR>(A, tw);
+        StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS * R, REM / R, TWL, NTHR>::run(A, tw);
+    }
+};
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int TWL, int NTHR>
+struct StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL, NTHR> {
+    static __device__ __forceinline__ void run(C*, const C*) {}
+};
+
 // Block sizes: rows per block of the x passes (~16 KB of complex data per
-// buffer), columns per block of the y/z passes (two L x KB buffers in 96 KB).
+// buffer, two buffers, 256 threads); columns per block of the y/z passes: KB
+// columns (up to 16, i.e. 128-byte row segments in float32) of length L in one
+// in-place buffer of at most 64 KB (three blocks per SM), NTC threads (16
+// elements each).
 template <typename T, int L> struct FftGeom {
     typedef typename C2<T>::t C;
     static constexpr int M = L / 2, MH = M + 1;
     static constexpr int RB0 = int(16384 / (sizeof(C) * M));
     static constexpr int RB = RB0 < 1 ? 1 : (RB0 > 64 ? 64 : RB0);
-    static constexpr int KLIM = int(98304 / (2 * sizeof(C) * L));
+    static constexpr int KLIM = int(65536 / (sizeof(C) * L));
     static constexpr int KB = KLIM >= 16 ? 16 : KLIM >= 8 ? 8 : KLIM >= 4 ? 4 : KLIM >= 2 ? 2 : 1;
+    static constexpr int NTC0 = (L * KB / 16 + 31) / 32 * 32;
+    static constexpr int NTC = NTC0 < 64 ? 64 : (NTC0 > 1024 ? 1024 : NTC0);
     static constexpr size_t smem_x = (size_t(2) * RB * M + L) * sizeof(C);
-    static constexpr size_t smem_c = (size_t(2) * L * KB + L) * sizeof(C);
+    static constexpr size_t smem_c = (size_t(L) * KB + L) * sizeof(C);
 };
 
 template <typename C, int L>
@@ -263,21 +328,22 @@ __global__ void __launch_bounds__(256) fft_x_inverse(const typename C2<T>::t* __
 // inverse: L inputs, P outputs)
 // ---------------------------------------------------------------------------
 template <typename T, int L, int P, bool INV>
-__global__ void __launch_bounds__(256) fft_y(typename C2<T>::t* __restrict__ spec,
-                                             const typename C2<T>::t* __restrict__ tw, size_t bs_spec) {
+__global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_y(typename C2<T>::t* __restrict__ spec,
+                                                            const typename C2<T>::t* __restrict__ tw,
+                                                            size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
-    constexpr int MH = Gm::MH, KB = Gm::KB;
+    constexpr int MH = Gm::MH, KB = Gm::KB, NTC = Gm::NTC;
     constexpr int NIN = INV ? L : P, NOUT = INV ? P : L;
     spec += blockIdx.z * bs_spec;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
-    C* B = A + L * KB;
-    C* tws = B + L * KB;
+    C* tws = A + L * KB;
     stage_twiddles<C, L>(tws, tw);
     const int k0 = blockIdx.x * KB;
     const size_t base = size_t(blockIdx.y) * L * MH;
-    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < L * KB; t += NTC) {
         const int c = t % KB, y = t / KB;
         C v;
         if (k0 + c < MH && y < NIN) v = spec[base + size_t(y) * MH + k0 + c];
@@ -285,10 +351,10 @@ __global__ void __launch_bounds__(256) fft_y(typename C2<T>::t* __restrict__ spe
         A[y * KB + c] = v;
     }
     __syncthreads();
-    C* R = Stockham<C, INV, L, KB, KB, 1, true, 1, L, L>::run(A, B, tws);
-    for (int t = threadIdx.x; t < NOUT * KB; t += blockDim.x) {
+    StockhamIP<C, INV, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
+    for (int t = threadIdx.x; t < NOUT * KB; t += NTC) {
         const int c = t % KB, y = t / KB;
-        if (k0 + c < MH) spec[base + size_t(y) * MH + k0 + c] = R[y * KB + c];
+        if (k0 + c < MH) spec[base + size_t(y) * MH + k0 + c] = A[y * KB + c];
     }
 }
 
@@ -300,24 +366,24 @@ __global__ void __launch_bounds__(256) fft_y(typename C2<T>::t* __restrict__ spe
 // even symmetry as gtab[kz'][ky'][kx], kz' = min(kz, L - kz), ky' likewise.
 // ---------------------------------------------------------------------------
 template <typename T, int L, int P, bool ISO>
-__global__ void __launch_bounds__(256) fft_z_solve(typename C2<T>::t* __restrict__ spec,
-                                                   const typename C2<T>::t* __restrict__ tw,
-                                                   const T* __restrict__ asin2, T coef,
-                                                   const T* __restrict__ gtab, size_t bs_spec) {
+__global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_solve(typename C2<T>::t* __restrict__ spec,
+                                                                  const typename C2<T>::t* __restrict__ tw,
+                                                                  const T* __restrict__ asin2, T coef,
+                                                                  const T* __restrict__ gtab, size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
-    constexpr int MH = Gm::MH, KB = Gm::KB;
+    constexpr int MH = Gm::MH, KB = Gm::KB, NTC = Gm::NTC;
     spec += blockIdx.z * bs_spec;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
-    C* B = A + L * KB;
-    C* tws = B + L * KB;
+    C* tws = A + L * KB;
     stage_twiddles<C, L>(tws, tw);
     const int k0 = blockIdx.x * KB;
     const int y = blockIdx.y;
     constexpr size_t zs = size_t(L) * MH;
     const size_t base = size_t(y) * MH;
-    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < L * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
         C v;
         if (k0 + c < MH && z < P) v = spec[base + size_t(z) * zs + k0 + c];
@@ -325,13 +391,12 @@ __global__ void __launch_bounds__(256) fft_z_solve(typename C2<T>::t* __restrict
         A[z * KB + c] = v;
     }
     __syncthreads();
-    C* R = Stockham<C, false, L, KB, KB, 1, true, 1, L, L>::run(A, B, tws);
-    C* S = (R == A) ? B : A;
+    StockhamIP<C, false, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
     const int ys = y <= L / 2 ? y : L - y;
-    for (int t = threadIdx.x; t < L * KB; t += blockDim.x) {
+    for (int t = threadIdx.x; t < L * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
         const int kx = k0 + c;
-        C v = R[z * KB + c];
+        C v = A[z * KB + c];
         if (kx < MH) {
             T g;
             if (ISO) {
@@ -346,13 +411,13 @@ __global__ void __launch_bounds__(256) fft_z_solve(typename C2<T>::t* __restrict
             v.x *= g;
             v.y *= g;
         }
-        S[z * KB + c] = v;
+        A[z * KB + c] = v;   // each element is read and written by the same thread
     }
     __syncthreads();
-    C* Q = Stockham<C, true, L, KB, KB, 1, true, 1, L, L>::run(S, R, tws);
-    for (int t = threadIdx.x; t < P * KB; t += blockDim.x) {
+    StockhamIP<C, true, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
+    for (int t = threadIdx.x; t < P * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
-        if (k0 + c < MH) spec[base + size_t(z) * zs + k0 + c] = Q[z * KB + c];
+        if (k0 + c < MH) spec[base + size_t(z) * zs + k0 + c] = A[z * KB + c];
     }
 }
 
