@@ -12,7 +12,7 @@ collected in ``READINGS`` and cited where they are used.
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -53,7 +53,10 @@ READINGS = {
     "s6": "Poisson zero mode Phi_hat_0 = 0 (mean-free potential).",
     "s7": "Poisson boundary periodic; 'isolated' mode is the zero-padded (2N)^3 "
           "convolution with g(r) = -G h^3/|r|, g(0) = -G h^2 * 2.3800774.",
-    "s8": "Hydro boundaries periodic.",
+    "s8": "Hydro boundaries periodic; 'outflow' mode (zero gradient): two layers of "
+          "ghost cells along each axis copy the nearest edge cell of the time-n state "
+          "and potential; the step is computed on the extended grid and cropped, so "
+          "ghost cells take the Eulerian stage from their own (ghost) neighbours.",
     "s9": "Gravity: central difference of Phi^n with rho^n, m^n, n^n, q^n.",
     "s10": "CFL: tau = C h / max over cells and axes of (|v_d| + sqrt(gamma p/rho)) "
            "and (|u_d| + sqrt(3 Pi_dd / n)).",
@@ -79,6 +82,7 @@ class Params:
     courant: float = 0.2       # Courant number of the CFL step (reading s10)
     eta: float = 1e-3          # energy-balance switch (reading s11)
     poisson: str = "periodic"  # "periodic" (s5/s6) or "isolated" (s7)
+    boundary: str = "periodic" # hydro boundaries: "periodic" or "outflow" (s8)
 
 
 # --------------------------------------------------------------------------
@@ -220,6 +224,16 @@ def cfl_dt(st, prm: Params):
 # --------------------------------------------------------------------------
 # one step of both fluids given Phi^n and tau
 # --------------------------------------------------------------------------
+def _extend(a, m):
+    """Zero-gradient extension by m cells on each side of the three grid axes (s8)."""
+    pad = [(0, 0)] * (a.ndim - 3) + [(m, m)] * 3
+    return np.pad(a, pad, mode="edge")
+
+
+def _crop(a, m):
+    return a[..., m:-m, m:-m, m:-m]
+
+
 def advance(st, phi, tau, prm: Params):
     """Eulerian stage, Lagrangian stage and energy balance of both fluids.
 
@@ -227,6 +241,14 @@ def advance(st, phi, tau, prm: Params):
     kappa_gas and kappa_bme (Sec. 2.4, times h^3) measured on the post-Lagrangian
     state before the balance.
     """
+    if prm.boundary == "outflow":
+        # reading s8: the update of a cell reaches 2 cells, so 2 ghost layers
+        # make the periodic shifts below act as the zero-gradient boundary
+        ext = {f: _extend(st[f], 2) for f in FIELDS}
+        new, kap = advance(ext, _extend(phi, 2), tau, replace(prm, boundary="periodic"))
+        return {f: _crop(new[f], 2) for f in FIELDS}, {k: _crop(v, 2) for k, v in kap.items()}
+    if prm.boundary != "periodic":
+        raise ValueError(prm.boundary)
     h, g, eta = prm.h, prm.gamma, prm.eta
     r = tau / h
     gphi = {d: (_up(phi, d) - _dn(phi, d)) / (2.0 * h) for d in DIRS}   # reading s9
@@ -317,20 +339,36 @@ def _wrap_take(a, idx, axis):
     return np.take(a, idx % a.shape[axis], axis=axis)
 
 
+def _clamp_take(a, idx, axis):
+    return np.take(a, np.clip(idx, 0, a.shape[axis] - 1), axis=axis)
+
+
 def advance_window(st, phi, tau, prm: Params, *, zslab=None, cells=None):
-    """``advance`` evaluated on part of a periodic grid.
+    """``advance`` evaluated on part of a grid.
 
     The update of a cell depends only on cells within L1 distance 2 (faces of its
-    neighbours), so a periodic window with a margin of 2 reproduces it exactly.
+    neighbours), so a window with a margin of 2 reproduces it exactly: indices
+    wrap on a periodic grid and clamp to the edge (ghost copies, s8) on an
+    outflow grid.
 
     zslab=(k0, k1): returns the new state on planes k0..k1-1 (full x, y extent).
     cells=(S, 3) int array of (k, j, i): returns the new state at those cells, shape (S,).
     """
+    outflow = prm.boundary == "outflow"
+    take = _clamp_take if outflow else _wrap_take
     if zslab is not None:
         k0, k1 = zslab
         kk = np.arange(k0 - 2, k1 + 2)
-        win = {f: _wrap_take(st[f], kk, 0) for f in FIELDS}
-        pw = _wrap_take(phi, kk, 0)
+        win = {f: take(st[f], kk, 0) for f in FIELDS}
+        pw = take(phi, kk, 0)
+        if outflow:
+            # z already holds its ghost planes; x and y get theirs here
+            pad = ((0, 0), (2, 2), (2, 2))
+            win = {f: np.pad(a, pad, mode="edge") for f, a in win.items()}
+            pw = np.pad(pw, pad, mode="edge")
+            new, kap = advance(win, pw, tau, replace(prm, boundary="periodic"))
+            return ({f: new[f][2:-2, 2:-2, 2:-2] for f in FIELDS},
+                    {k: v[2:-2, 2:-2, 2:-2] for k, v in kap.items()})
         new, kap = advance(win, pw, tau, prm)
         return {f: new[f][2:-2] for f in FIELDS}, {k: v[2:-2] for k, v in kap.items()}
     cells = np.asarray(cells)
@@ -341,10 +379,12 @@ def advance_window(st, phi, tau, prm: Params, *, zslab=None, cells=None):
 
     def cut(a):
         nz, ny, nx = a.shape
+        if outflow:
+            return a[np.clip(K, 0, nz - 1), np.clip(J, 0, ny - 1), np.clip(I, 0, nx - 1)]
         return a[K % nz, J % ny, I % nx]
 
     win = {f: cut(st[f]) for f in FIELDS}
-    new, kap = advance(win, cut(phi), tau, prm)
+    new, kap = advance(win, cut(phi), tau, replace(prm, boundary="periodic"))
     return {f: new[f][:, 2, 2, 2] for f in FIELDS}, {k: v[:, 2, 2, 2] for k, v in kap.items()}
 
 
