@@ -3,7 +3,7 @@
  *
  * The library advances a self-gravitating adiabatic gas and a collisionless
  * "Boltzmann-moment" fluid (density, momentum, full symmetric energy and
- * velocity-dispersion tensors) on a periodic uniform N^3 grid by the scheme of
+ * velocity-dispersion tensors) on a uniform N^3 grid (periodic or outflow) by the scheme of
  * Kulikov 2013 (GPUPEGAS):
  *   Sec. 2.3  Poisson equation for the total potential, Laplace(Phi) = 4 pi G (rho + n),
  *             solved by FFT with the 27-point stencil symbol;
@@ -62,7 +62,18 @@ enum flic_poisson_bc {
     FLIC_PERIODIC = 0,   /* periodic potential, 27-point symbol (Sec. 2.3) */
     FLIC_ISOLATED = 1    /* vacuum boundaries: zero-padded (2N)^3 convolution with the point-mass
                             Green's function -G h^3/|r|, -G h^2 (3 ln(2+sqrt 3) - pi/2) at r = 0
-                            (n = 8..128, 256, 512); the hydrodynamics stays periodic */
+                            (n = 8..128, 256, 512) */
+};
+
+/* Hydrodynamic boundaries.  The paper states none; periodic is the default
+ * reading.  Outflow (zero gradient): two layers of ghost cells along each axis
+ * copy the nearest edge cell of the time-n state and potential, and the step is
+ * computed as on the grid extended by them (ghost cells take the Eulerian stage
+ * from their own ghost neighbours); mass and momentum then change by the
+ * boundary fluxes. */
+enum flic_hydro_bc {
+    FLIC_HYDRO_PERIODIC = 0,
+    FLIC_HYDRO_OUTFLOW = 1
 };
 
 typedef struct flic_grid_desc {
@@ -75,6 +86,7 @@ typedef struct flic_grid_desc {
     double eta;          /* energy-balance switch (1e-3) */
     int precision;       /* enum flic_precision */
     int poisson_bc;      /* enum flic_poisson_bc */
+    int hydro_bc;        /* enum flic_hydro_bc (0: periodic) */
 } flic_grid_desc;
 
 /* Per-step record.  Conserved sums describe the state at the START of the step

@@ -102,6 +102,7 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
     a.phi = reinterpret_cast<const T*>(h->phi);
     a.fs = h->fs;
     a.n = h->N;
+    a.outflow = h->d.hydro_bc == FLIC_HYDRO_OUTFLOW;
     a.tau = h->scal + S_TAU;
     a.inv_h = 1.0 / h->h;
     a.gamma = T(h->d.gamma);
@@ -296,6 +297,7 @@ int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out) 
     }
     if (desc->precision != FLIC_FP64 && desc->precision != FLIC_MIXED) { g_init_err = "unknown precision"; return FLIC_ERR_INVALID_ARG; }
     if (desc->poisson_bc != FLIC_PERIODIC && desc->poisson_bc != FLIC_ISOLATED) { g_init_err = "unknown Poisson boundary"; return FLIC_ERR_INVALID_ARG; }
+    if (desc->hydro_bc != FLIC_HYDRO_PERIODIC && desc->hydro_bc != FLIC_HYDRO_OUTFLOW) { g_init_err = "unknown hydro boundary"; return FLIC_ERR_INVALID_ARG; }
     flic_handle* h = new flic_handle();
     h->d = *desc;
     h->N = desc->n;

@@ -102,10 +102,10 @@ int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
     }
     if (ev) ENS_CK(e, cudaEventRecord(ev[1], e->st));
     ENS_CK(e, launch_gas_batch<T>(reinterpret_cast<const StencilArgs<T>*>(e->tab_gas[e->cur]), e->work_gas,
-                                  e->nwork_gas, e->st));
+                                  e->nwork_gas, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[2], e->st));
     ENS_CK(e, launch_bme_batch<T>(reinterpret_cast<const StencilArgs<T>*>(e->tab_bme[e->cur]), e->work_bme,
-                                  e->nwork_bme, e->st));
+                                  e->nwork_bme, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[3], e->st));
     ENS_CK(e, step_finalize_batch(e->fin_tab, e->nruns, 1, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[4], e->st));
@@ -273,6 +273,7 @@ int ens_init(flic_ensemble* e) {
             a.phi = reinterpret_cast<const T*>(c.phi) + size_t(s) * c.fs;
             a.fs = c.fs;
             a.n = c.N;
+            a.outflow = e->d.hydro_bc == FLIC_HYDRO_OUTFLOW;
             a.tau = sc + S_TAU;
             a.inv_h = 1.0 / c.h;
             a.gamma = T(e->d.gamma);
@@ -358,7 +359,8 @@ int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, f
     const flic_grid_desc& d0 = descs[0];
     for (int r = 0; r < nruns; ++r) {
         const flic_grid_desc& d = descs[r];
-        if (d.precision != d0.precision || d.poisson_bc != d0.poisson_bc || d.gamma != d0.gamma || d.G != d0.G ||
+        if (d.precision != d0.precision || d.poisson_bc != d0.poisson_bc || d.hydro_bc != d0.hydro_bc ||
+            d.gamma != d0.gamma || d.G != d0.G ||
             d.courant != d0.courant || d.eta != d0.eta || d.box_min != d0.box_min || d.box_max != d0.box_max) {
             set_global_error("ensemble runs must share every constant except n");
             return FLIC_ERR_INVALID_ARG;
@@ -373,7 +375,8 @@ int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, f
     }
     if (!(d0.box_max > d0.box_min) || !(d0.gamma > 1.0) || !(d0.courant > 0.0) || !(d0.G >= 0.0) ||
         (d0.precision != FLIC_FP64 && d0.precision != FLIC_MIXED) ||
-        (d0.poisson_bc != FLIC_PERIODIC && d0.poisson_bc != FLIC_ISOLATED)) {
+        (d0.poisson_bc != FLIC_PERIODIC && d0.poisson_bc != FLIC_ISOLATED) ||
+        (d0.hydro_bc != FLIC_HYDRO_PERIODIC && d0.hydro_bc != FLIC_HYDRO_OUTFLOW)) {
         set_global_error("invalid ensemble constants");
         return FLIC_ERR_INVALID_ARG;
     }

@@ -26,9 +26,11 @@ template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const Step
 template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
 // One launch over a work list spanning several runs (table and work in device memory).
 template <typename T>
-cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st);
+cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
+                             cudaStream_t st);
 template <typename T>
-cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st);
+cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
+                             cudaStream_t st);
 
 // float64 <-> storage precision conversion of one field.
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);

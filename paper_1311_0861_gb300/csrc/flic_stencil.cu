@@ -37,7 +37,7 @@ StepCfg make_cfg(int N, int tz) {
         int dev = 0, sms = 152, per_sm = 1;
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_step_kernel<P, T, C>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_step_kernel<P, T, C, false>,
                                                       c.threads, c.smem);
         if (per_sm < 1) per_sm = 1;
         const long slots = long(sms) * per_sm;
@@ -59,25 +59,34 @@ StepCfg make_cfg(int N, int tz) {
 
 template <class P, typename T, class C>
 cudaError_t prepare() {
-    return cudaFuncSetAttribute(fluid_step_kernel<P, T, C>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fluid_step_kernel<P, T, C, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geom<P, T, C>::smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fluid_step_kernel<P, T, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geom<P, T, C>::smem_bytes);
 }
 
 template <class P, typename T, class C>
 cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
     BatchArgs<T> none{nullptr, nullptr};
-    fluid_step_kernel<P, T, C>
-        <<<dim3(c.tiles_x * c.tiles_y, c.blocks_z), c.threads, c.smem, st>>>(a, none);
+    const dim3 grid(c.tiles_x * c.tiles_y, c.blocks_z);
+    if (a.outflow)
+        fluid_step_kernel<P, T, C, true><<<grid, c.threads, c.smem, st>>>(a, none);
+    else
+        fluid_step_kernel<P, T, C, false><<<grid, c.threads, c.smem, st>>>(a, none);
     return cudaGetLastError();
 }
 
 template <class P, typename T, class C>
-cudaError_t launch_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
+cudaError_t launch_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
+                         cudaStream_t st) {
     StencilArgs<T> unused{};
     BatchArgs<T> b{table, work};
-    fluid_step_kernel<P, T, C>
-        <<<nwork, Geom<P, T, C>::NTH, Geom<P, T, C>::smem_bytes, st>>>(unused, b);
+    if (outflow)
+        fluid_step_kernel<P, T, C, true><<<nwork, Geom<P, T, C>::NTH, Geom<P, T, C>::smem_bytes, st>>>(unused, b);
+    else
+        fluid_step_kernel<P, T, C, false><<<nwork, Geom<P, T, C>::NTH, Geom<P, T, C>::smem_bytes, st>>>(unused, b);
     return cudaGetLastError();
 }
 
@@ -97,18 +106,19 @@ template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const Step
 }
 
 template <typename T>
-cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
-    return launch_batch<GasPhys<T>, T, typename Tiles<T>::Gas>(table, work, nwork, st);
+cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
+                             cudaStream_t st) {
+    return launch_batch<GasPhys<T>, T, typename Tiles<T>::Gas>(table, work, nwork, outflow, st);
 }
 template <typename T>
-cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, cudaStream_t st) {
-    return launch_batch<BmePhys<T>, T, typename Tiles<T>::Bme>(table, work, nwork,
-                                                                                              st);
+cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
+                             cudaStream_t st) {
+    return launch_batch<BmePhys<T>, T, typename Tiles<T>::Bme>(table, work, nwork, outflow, st);
 }
-template cudaError_t launch_gas_batch<float>(const StencilArgs<float>*, const WorkItem*, int, cudaStream_t);
-template cudaError_t launch_gas_batch<double>(const StencilArgs<double>*, const WorkItem*, int, cudaStream_t);
-template cudaError_t launch_bme_batch<float>(const StencilArgs<float>*, const WorkItem*, int, cudaStream_t);
-template cudaError_t launch_bme_batch<double>(const StencilArgs<double>*, const WorkItem*, int, cudaStream_t);
+template cudaError_t launch_gas_batch<float>(const StencilArgs<float>*, const WorkItem*, int, bool, cudaStream_t);
+template cudaError_t launch_gas_batch<double>(const StencilArgs<double>*, const WorkItem*, int, bool, cudaStream_t);
+template cudaError_t launch_bme_batch<float>(const StencilArgs<float>*, const WorkItem*, int, bool, cudaStream_t);
+template cudaError_t launch_bme_batch<double>(const StencilArgs<double>*, const WorkItem*, int, bool, cudaStream_t);
 
 template <typename T> cudaError_t stencil_prepare() {
     cudaError_t e = prepare<GasPhys<T>, T, typename Tiles<T>::Gas>();

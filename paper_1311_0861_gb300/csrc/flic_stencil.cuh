@@ -48,6 +48,7 @@ struct StencilArgs {
     int n;                    // cells per axis
     int tz;                   // z planes per block
     int tiles_x;              // blocks along x (ceil(n / TX))
+    int outflow;              // hydro boundaries: 0 periodic wrap, 1 zero-gradient ghost cells
     const double* tau;        // step size (device scalar)
     double inv_h;             // 1 / h
     T gamma, eta;
@@ -376,12 +377,13 @@ struct Geom {
     static constexpr size_t ex_slot = size_t(P::NEX) * H1 * W2;
     static constexpr size_t ex_elems = SEX ? 2 * ex_slot : 0;
     // the double-precision reduction scratch starts on a 16-byte boundary,
-    // followed by the wrapped-coordinate tables (CPR + H2 ints)
+    // followed by the coordinate tables (CPR + H2 ints, then CPR more used by
+    // the outflow kernels)
     static constexpr size_t red_offset =
         ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems + ex_elems) * sizeof(T) + 15) /
         16 * 16;
     static constexpr size_t tab_offset = red_offset + sizeof(double) * 32 * (P::NQ + 1);
-    static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (CPR + H2);
+    static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (2 * CPR + H2);
 };
 
 // Updated cell i -> R1 coordinates (jx, jy): tile cells first (so that thread i
@@ -416,7 +418,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 __device__ __forceinline__ int ring_slot(int p) { return ((p % RING_SLOTS) + RING_SLOTS) % RING_SLOTS; }
 
-template <class P, typename T, class C>
+// OUT: outflow hydro boundaries -- indices clamp to the edge instead of
+// wrapping, so the ring holds two layers of ghost copies of the edge cells
+// (zero gradient) and the step acts as on the grid extended by them.
+template <class P, typename T, class C, bool OUT>
 __global__ void __launch_bounds__(Geom<P, T, C>::NTH, C::MINB)
 fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     using Gm = Geom<P, T, C>;
@@ -439,6 +444,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     double* red = reinterpret_cast<double*>(smem_raw + Gm::red_offset);
     int* xoff = reinterpret_cast<int*>(smem_raw + Gm::tab_offset);   // wrapped x of each 8-byte column chunk
     int* yoff = xoff + CPR;                                            // wrapped y * N of R2 rows
+    int* xlast = yoff + H2;   // outflow: x of the last element of each chunk (ghost chunks repeat the edge)
 
     const int tid = threadIdx.x;
     int tile, chunk, prow;
@@ -467,8 +473,18 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     const T gamma = a.gamma, eta = a.eta;
 
     // x0 - 2 and N are multiples of CH, so no chunk straddles the periodic wrap
-    for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
-    for (int i = tid; i < H2; i += NTH) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
+    // or the domain edge: with outflow a chunk lies inside the grid or wholly
+    // in the ghost layers (all its elements then copy one edge cell)
+    if constexpr (OUT) {
+        for (int i = tid; i < CPR; i += NTH) {
+            xoff[i] = min(max(x0 - 2 + CH * i, 0), N - 1);
+            xlast[i] = min(max(x0 - 2 + CH * i + CH - 1, 0), N - 1);
+        }
+        for (int i = tid; i < H2; i += NTH) yoff[i] = min(max(y0 + i - 2, 0), N - 1) * N;
+    } else {
+        for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
+        for (int i = tid; i < H2; i += NTH) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
+    }
     __syncthreads();
 
     // own tile cell (threads tid < NT)
@@ -481,15 +497,34 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     // (tile + 2-cell halo) into its ring slot, committed as one group.  Each
     // thread owns fixed (row, chunk) positions and walks the fields.
     constexpr int NPOS = H2 * CPR;
+    auto plane_of = [&](int pz) {
+        if constexpr (OUT) return min(max(pz, 0), N - 1);
+        return pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
+    };
+    // a ghost chunk at an outflow edge (its elements all copy one edge cell)
+    auto ghost_chunk = [&](int c) { return OUT && CH > 1 && xlast[c] != xoff[c] + CH - 1; };
     auto issue_plane = [&](int pz) {
         T* dst = ring + ring_slot(pz) * NR * R2;
-        const int zw = pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
-        const size_t zoff = size_t(zw) * plane;
+        const size_t zoff = size_t(plane_of(pz)) * plane;
         for (int pos = tid; pos < NPOS; pos += NTH) {
             const int iy = pos / CPR, c = pos % CPR;
             T* d = dst + iy * W2 + c * CH;
             const size_t goff = zoff + size_t(yoff[iy]) + xoff[c];
             const T* src = a.in + goff;
+            if (ghost_chunk(c)) {
+                // plain loads (visible after the barrier that precedes this
+                // slot's first use, like the asynchronous copies)
+#pragma unroll
+                for (int r = 0; r < NR - 1; ++r) {
+                    const T v = __ldg(src + size_t(P::ring_field(r)) * a.fs);
+#pragma unroll
+                    for (int k = 0; k < CH; ++k) d[r * R2 + k] = v;
+                }
+                const T v = __ldg(a.phi + goff);
+#pragma unroll
+                for (int k = 0; k < CH; ++k) d[(NR - 1) * R2 + k] = v;
+                continue;
+            }
 #pragma unroll
             for (int r = 0; r < NR - 1; ++r) cp_async8(d + r * R2, src + size_t(P::ring_field(r)) * a.fs);
             cp_async8(d + (NR - 1) * R2, a.phi + goff);
@@ -501,19 +536,30 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     constexpr int NPOS1 = Gm::H1 * CPR;
     auto issue_extra = [&](int pz) {
         T* dst = exb + (pz & 1) * Gm::ex_slot;
-        const int zw = pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
-        const size_t zoff = size_t(zw) * plane;
+        const size_t zoff = size_t(plane_of(pz)) * plane;
         for (int pos = tid; pos < NPOS1; pos += NTH) {
             const int jy = pos / CPR, c = pos % CPR;
             T* d = dst + jy * W2 + c * CH;
             const T* src = a.in + zoff + size_t(yoff[jy + 1]) + xoff[c];
+            if (ghost_chunk(c)) {
+#pragma unroll
+                for (int k = 0; k < NEX; ++k) {
+                    const T v = __ldg(src + size_t(P::extra_field(k)) * a.fs);
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) d[k * Gm::H1 * W2 + j] = v;
+                }
+                continue;
+            }
 #pragma unroll
             for (int k = 0; k < NEX; ++k)
                 cp_async8(d + k * Gm::H1 * W2, src + size_t(P::extra_field(k)) * a.fs);
         }
     };
-    // global x of R2 column ix (chunks never straddle the wrap)
-    auto gx = [&](int ix) { return xoff[ix / CH] + ix % CH; };
+    // global x of R2 column ix (chunks never straddle the wrap or the edge)
+    auto gx = [&](int ix) {
+        if constexpr (OUT) return ghost_chunk(ix / CH) ? xoff[ix / CH] : xoff[ix / CH] + ix % CH;
+        return xoff[ix / CH] + ix % CH;
+    };
 
     const size_t own_g = size_t(yoff[own_ty + 2]) + gx(own_tx + 2);
     T fprev[NF], acc[NF];
@@ -581,7 +627,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         const bool active = (e >= z0 - 1);   // f' of plane e is needed
         // ---- phase 1: z face e+1/2 and Eulerian update of plane e over R1 ----
         {
-            const size_t zoff_e = size_t(e < 0 ? e + N : (e >= N ? e - N : e)) * plane;
+            const size_t zoff_e = size_t(plane_of(e)) * plane;
             for (int i = tid; i < NU; i += NTH) {
                 int jx, jy;
                 r1_coords<TX, TY>(i, jx, jy);

@@ -25,6 +25,7 @@ NFIELDS = 22
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5
 FP64, MIXED = 0, 1
 PERIODIC, ISOLATED = 0, 1
+HYDRO_PERIODIC, HYDRO_OUTFLOW = 0, 1
 
 # every entry point declared in include/flic.h
 EXPORTS = ("flic_init_grid", "flic_set_state", "flic_set_state_device", "flic_get_state",
@@ -42,7 +43,8 @@ STAGES = ("poisson", "gas", "bme", "finalize")
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("box_min", ctypes.c_double), ("box_max", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("G", ctypes.c_double), ("courant", ctypes.c_double),
-                ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("poisson_bc", ctypes.c_int)]
+                ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("poisson_bc", ctypes.c_int),
+                ("hydro_bc", ctypes.c_int)]
 
 
 class Diag(ctypes.Structure):
@@ -167,16 +169,19 @@ def state_diagnostics_noalloc(fields, phi, n: int, h: float, gamma: float = 5.0 
 
 
 class Grid:
-    """One periodic N^3 grid of the two-fluid step (a libflic handle)."""
+    """One N^3 grid of the two-fluid step (a libflic handle).  ``poisson``:
+    "periodic" or "isolated" gravity; ``boundary``: "periodic" or "outflow" hydro."""
 
     def __init__(self, n: int, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
-                 precision: str = "fp64", poisson: str = "periodic", stream: int = 0):
+                 precision: str = "fp64", poisson: str = "periodic", boundary: str = "periodic",
+                 stream: int = 0):
         self.lib = load()
         self.n = int(n)
         self.h = (box[1] - box[0]) / n
         d = GridDesc(int(n), box[0], box[1], gamma, G, courant, eta,
                      {"fp64": FP64, "mixed": MIXED}[precision],
-                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson])
+                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson],
+                     {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary])
         self._h = ctypes.c_void_p()
         rc = self.lib.flic_init_grid(ctypes.byref(d), ctypes.c_void_p(stream or None), ctypes.byref(self._h))
         if rc != OK:
@@ -294,12 +299,14 @@ class Ensemble:
     """Independent runs of uneven sizes advanced together (a libflic ensemble)."""
 
     def __init__(self, sizes, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
-                 precision: str = "mixed", poisson: str = "periodic", stream: int = 0):
+                 precision: str = "mixed", poisson: str = "periodic", boundary: str = "periodic",
+                 stream: int = 0):
         self.lib = load()
         self.sizes = [int(n) for n in sizes]
+        hb = {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary]
         descs = (GridDesc * len(self.sizes))(*[
             GridDesc(n, box[0], box[1], gamma, G, courant, eta, {"fp64": FP64, "mixed": MIXED}[precision],
-                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson]) for n in self.sizes])
+                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson], hb) for n in self.sizes])
         self._e = ctypes.c_void_p()
         rc = self.lib.flic_ensemble_create(descs, len(self.sizes), ctypes.c_void_p(stream or None),
                                            ctypes.byref(self._e))

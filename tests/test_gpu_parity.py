@@ -232,3 +232,50 @@ def test_steps_isolated_fp64(flic, N):
     err = rel_l1(out, ref)
     assert max(err.values()) <= 1e-10, err
     assert abs(d["epot"] - rrec[-1]["epot"]) <= 1e-11 * abs(rrec[-1]["epot"])
+
+
+@pytest.mark.parametrize("N,poisson,rough", [(8, "isolated", True), (12, "periodic", False), (24, "isolated", True),
+                                             (48, "isolated", False), (64, "periodic", True)])
+def test_one_step_outflow_fp64(flic, N, poisson, rough):
+    """Outflow (zero-gradient) hydro boundaries: ghost copies of the edge cells,
+    partial tiles and ragged z chunks at every face of the box."""
+    s = I.random_state((N, N, N), seed=80 + N, rough=rough)
+    prm = O.Params(h=s.h, gamma=s.gamma, poisson=poisson, boundary="outflow")
+    ref, rrec = O.run(s.state, prm, 1)
+    with flic.Grid(N, precision="fp64", gamma=s.gamma, poisson=poisson, boundary="outflow",
+                   box=(-1.0, -1.0 + s.h * N)) as g:
+        g.set_state(s.state)
+        g.step()
+        out = g.get_state()
+        d = g.step_diagnostics()
+    err = max_rel(out, ref)
+    assert max(err.values()) <= 1e-11, err
+    r = rrec[-1]
+    assert abs(d["dt"] - r["dt"]) <= 1e-14 * r["dt"]
+    for k in ("mass_gas", "mass_bme", "kappa_gas", "kappa_bme", "vmax", "epot"):
+        assert abs(d[k] - r[k]) <= 1e-11 * max(abs(r[k]), 1e-300), (k, d[k], r[k])
+
+
+def test_outflow_mixed_ten_steps(flic):
+    s = I.head_on(32)
+    prm = O.Params(h=s.h, gamma=s.gamma, poisson="isolated", boundary="outflow")
+    ref, _ = O.run(s.state, prm, 10)
+    with flic.Grid(32, precision="mixed", gamma=s.gamma, poisson="isolated", boundary="outflow") as g:
+        g.set_state(s.state)
+        g.run(10)
+        out = g.get_state()
+    err = rel_l1(out, ref)
+    assert err["rho"] <= 1e-4 and err["n"] <= 1e-4, err
+
+
+def test_outflow_ten_steps_fp64_graph(flic):
+    s = I.random_state((24, 24, 24), seed=91)
+    prm = O.Params(h=s.h, gamma=s.gamma, poisson="isolated", boundary="outflow")
+    ref, _ = O.run(s.state, prm, 10)
+    with flic.Grid(24, precision="fp64", gamma=s.gamma, poisson="isolated", boundary="outflow",
+                   box=(-1.0, -1.0 + s.h * 24)) as g:
+        g.set_state(s.state)
+        g.run(10)
+        out = g.get_state()
+    err = rel_l1(out, ref)
+    assert max(err.values()) <= 1e-10, err
