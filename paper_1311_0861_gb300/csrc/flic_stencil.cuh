@@ -30,6 +30,8 @@
 // live in registers of the thread that owns the column.
 #pragma once
 
+#include <type_traits>
+
 #include "flic_common.cuh"
 
 namespace flic {
@@ -570,6 +572,29 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     T vmax = T(0);
     bool bad = false;
 
+    // Fields the Eulerian update reads straight from global memory (SEX false):
+    // with one updated cell per thread (NTH >= NU) each thread keeps its cell
+    // for the whole march, so the next plane's values are loaded into
+    // registers one iteration ahead and their latency hides behind a plane.
+    constexpr bool PREF = !SEX && NEX > 0 && NTH >= NU;
+    T exn[NEX > 0 ? NEX : 1];
+    size_t my_g = 0;
+    if constexpr (PREF) {
+        if (tid < NU) {
+            int jx, jy;
+            r1_coords<TX, TY>(tid, jx, jy);
+            my_g = size_t(yoff[jy + 1]) + gx(jx + 1);
+        }
+    }
+    auto load_ex = [&](int pz) {
+        const size_t g = size_t(plane_of(pz)) * plane + my_g;
+#pragma unroll
+        for (int k = 0; k < NEX; ++k) exn[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
+    };
+    if constexpr (PREF) {
+        if (tid < NU) load_ex(z0 - 1);   // the first plane whose update is needed
+    }
+
     // x / y face solutions of plane pe over the tile + 1-cell halo (S1).  The
     // helpers take the first NH * HR faces (they have no S3 work); the rest go
     // round-robin over all threads.
@@ -635,7 +660,11 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 const int c2 = (jy + 1) * W2 + jx + 1;
                 T ex[NEX > 0 ? NEX : 1];
                 if (active) {
-                    if (SEX) {
+                    if constexpr (PREF) {
+#pragma unroll
+                        for (int k = 0; k < NEX; ++k) ex[k] = exn[k];
+                        if (e + 1 <= z1) load_ex(e + 1);
+                    } else if (SEX) {
                         const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
 #pragma unroll
                         for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
@@ -693,15 +722,43 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
             const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
             T out[NF];
+            if constexpr (std::is_same<T, float>::value && NF % 2 == 0) {
+                // fields in pairs with packed float32 arithmetic (one instruction
+                // for two fields); the same operations as the scalar form below
+                const float2 wz = make_float2(Wzm, Wzm), nr = make_float2(-rat, -rat), pr = make_float2(rat, rat);
+                const float2 wxp = make_float2(Wxp, Wxp), nwxm = make_float2(-Wxm, -Wxm);
+                const float2 wyp = make_float2(Wyp, Wyp), nwym = make_float2(-Wym, -Wym);
+                const bool zup = Wzm > T(0);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const T* F = fpb + f * R1;
-                const T fc = F[own_c1];
-                const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
-                const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
-                out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
-                acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
-                fprev[f] = fc;
+                for (int f = 0; f < NF; f += 2) {
+                    const T* F0 = fpb + f * R1;
+                    const T* F1 = F0 + R1;
+                    const float2 fc = make_float2(F0[own_c1], F1[own_c1]);
+                    const float2 uxm = make_float2(F0[cxm], F1[cxm]), uxp = make_float2(F0[cxp], F1[cxp]);
+                    const float2 uym = make_float2(F0[cym], F1[cym]), uyp = make_float2(F0[cyp], F1[cyp]);
+                    const float2 Fzm = __fmul2_rn(wz, zup ? make_float2(fprev[f], fprev[f + 1]) : fc);
+                    const float2 o = __ffma2_rn(nr, Fzm, make_float2(acc[f], acc[f + 1]));   // completes plane e-1
+                    float2 t = __fadd2_rn(__ffma2_rn(nwxm, uxm, __fmul2_rn(wxp, uxp)),
+                                          __ffma2_rn(nwym, uym, __fmul2_rn(wyp, uyp)));
+                    const float2 n2 = __ffma2_rn(pr, Fzm, __ffma2_rn(nr, t, fc));
+                    out[f] = o.x;
+                    out[f + 1] = o.y;
+                    acc[f] = n2.x;
+                    acc[f + 1] = n2.y;
+                    fprev[f] = fc.x;
+                    fprev[f + 1] = fc.y;
+                }
+            } else {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T* F = fpb + f * R1;
+                    const T fc = F[own_c1];
+                    const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
+                    const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
+                    out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
+                    acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
+                    fprev[f] = fc;
+                }
             }
             const int l = e - 1;
             if (l >= z0 && l < z1 && own_valid) {
