@@ -87,6 +87,24 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Two accumulators advanced together: packed float32 two-sum (one instruction
+// per operation for both), plain adds in float64.
+__device__ __forceinline__ void acc_add2(Acc<double>& qa, Acc<double>& qb, double xa, double xb) {
+    qa.add(xa);
+    qb.add(xb);
+}
+__device__ __forceinline__ void acc_add2(Acc<float>& qa, Acc<float>& qb, float xa, float xb) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 S = make_float2(qa.s, qb.s), X = make_float2(xa, xb);
+    const float2 t = __fadd2_rn(S, X);
+    const float2 bb = __ffma2_rn(m1, S, t);                                  // t - s
+    const float2 e = __fadd2_rn(__ffma2_rn(m1, __ffma2_rn(m1, bb, t), S),    // s - (t - bb)
+                                __ffma2_rn(m1, bb, X));                       // x - bb
+    const float2 c = __fadd2_rn(make_float2(qa.c, qb.c), e);
+    qa.s = t.x; qb.s = t.y;
+    qa.c = c.x; qb.c = c.y;
+}
+
 // ---------------------------------------------------------------------------
 // physics policies
 // ---------------------------------------------------------------------------
@@ -148,12 +166,9 @@ struct GasPhys {
     static __device__ __forceinline__ void accumulate_input(const T* r, int c, int R2, Acc<T>* q) {
         T rho = r[0 * R2 + c];
         T mx = r[1 * R2 + c], my = r[2 * R2 + c], mz = r[3 * R2 + c];
-        q[0].add(rho);
-        q[1].add(mx);
-        q[2].add(my);
-        q[3].add(mz);
-        q[4].add(T(0.5) * (mx * mx + my * my + mz * mz) * rcp(rho));
-        q[5].add(r[5 * R2 + c]);
+        acc_add2(q[0], q[1], rho, mx);
+        acc_add2(q[2], q[3], my, mz);
+        acc_add2(q[4], q[5], T(0.5) * (mx * mx + my * my + mz * mz) * rcp(rho), r[5 * R2 + c]);
         q[6].add(T(0.5) * rho * r[R_PHI * R2 + c]);
     }
 
@@ -221,8 +236,6 @@ struct BmePhys {
         const T s3 = T(1.7320508075688772935274463);
         T rho = T(0.5) * (nL + nR);
         T A = T(0.5) * (PnnL + PnnR);
-        T b1 = T(0.5) * (P1L + P1R);
-        T b2 = T(0.5) * (P2L + P2R);
         T iz2 = rsq(rho * A);            // 1/sqrt(rho Pi_nn)
         T Z2 = rho * A * iz2;            // sqrt(rho Pi_nn)
         T Z1 = s3 * Z2;                  // sqrt(3 rho Pi_nn)
@@ -233,11 +246,31 @@ struct BmePhys {
         T cu = dPnn * (T(1) - s3) * iA * iz1;   // multiplies b_k in u_t
         T cp = dun * rho * (s3 - T(1)) * iz2;   // multiplies b_k in Pi_nt
         outv[d] = T(0.5) * (unL + unR) + dPnn * iz1;
-        outv[t1] = T(0.5) * (u1L + u1R) + T(0.5) * (P1L - P1R) * iz2 + b1 * cu;
-        outv[t2] = T(0.5) * (u2L + u2R) + T(0.5) * (P2L - P2R) * iz2 + b2 * cu;
         outv[3 + d] = A + dun * Z1;
-        outv[3 + t1] = b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp;
-        outv[3 + t2] = b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp;
+        if constexpr (std::is_same<T, float>::value) {
+            // the two tangents share every coefficient: one packed instruction
+            // per operation on (t1, t2)
+            const float2 h = make_float2(0.5f, 0.5f);
+            const float2 uL = make_float2(u1L, u2L), uR = make_float2(u1R, u2R);
+            const float2 PL = make_float2(P1L, P2L), PR = make_float2(P1R, P2R);
+            const float2 b = __fmul2_rn(h, __fadd2_rn(PL, PR));
+            const float2 hiz2 = make_float2(T(0.5) * iz2, T(0.5) * iz2), hZ2 = make_float2(T(0.5) * Z2, T(0.5) * Z2);
+            const float2 m1 = make_float2(-1.0f, -1.0f);
+            const float2 ut = __ffma2_rn(b, make_float2(cu, cu),
+                                         __ffma2_rn(__ffma2_rn(m1, PR, PL), hiz2, __fmul2_rn(h, __fadd2_rn(uL, uR))));
+            const float2 pt = __ffma2_rn(b, make_float2(cp, cp), __ffma2_rn(__ffma2_rn(m1, uR, uL), hZ2, b));
+            outv[t1] = ut.x;
+            outv[t2] = ut.y;
+            outv[3 + t1] = pt.x;
+            outv[3 + t2] = pt.y;
+        } else {
+            T b1 = T(0.5) * (P1L + P1R);
+            T b2 = T(0.5) * (P2L + P2R);
+            outv[t1] = T(0.5) * (u1L + u1R) + T(0.5) * (P1L - P1R) * iz2 + b1 * cu;
+            outv[t2] = T(0.5) * (u2L + u2R) + T(0.5) * (P2L - P2R) * iz2 + b2 * cu;
+            outv[3 + t1] = b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp;
+            outv[3 + t2] = b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp;
+        }
     }
 
     // nE: the cell's energy tensor (6 components, read directly from global memory)
@@ -285,6 +318,7 @@ struct BmePhys {
     static __device__ __forceinline__ void accumulate_input(const T* r, int c, int R2, Acc<T>* q) {
         T n = r[0 * R2 + c];
         T qx = r[1 * R2 + c], qy = r[2 * R2 + c], qz = r[3 * R2 + c];
+        // (scalar adds: pairing these measured slower in this kernel)
         q[0].add(n);
         q[1].add(qx);
         q[2].add(qy);
