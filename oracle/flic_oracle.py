@@ -42,7 +42,10 @@ CUBE_SELF_POTENTIAL = 3.0 * math.log(2.0 + math.sqrt(3.0)) - 0.5 * math.pi
 
 READINGS = {
     "s1": "Lagrangian flux (Sec. 2.1): F_{i+1/2} = W_{i+1/2} * f_upwind with W the "
-          "face velocity of the same face (reading A of the garbled 4-term average).",
+          "face velocity of the same face (reading A of the garbled 4-term average); "
+          "reading B (flux='B') takes the printed 4-term form literally: W is the mean "
+          "of the face velocities of the same face orientation at the four transverse "
+          "diagonal neighbours (k+-1, l+-1), and the upwind side follows its sign.",
     "s2": "Upwind tie W == 0 gives F = 0 either way.",
     "s3": "The transport velocity is the Eulerian-stage face solution at time n.",
     "s4": "Bracketed BME coefficients (Sec. 2.2) are arithmetic L/R means of n, "
@@ -83,6 +86,7 @@ class Params:
     eta: float = 1e-3          # energy-balance switch (reading s11)
     poisson: str = "periodic"  # "periodic" (s5/s6) or "isolated" (s7)
     boundary: str = "periodic" # hydro boundaries: "periodic" or "outflow" (s8)
+    flux: str = "A"            # Lagrangian transport velocity: reading "A" or "B" of s1
 
 
 # --------------------------------------------------------------------------
@@ -308,6 +312,10 @@ def advance(st, phi, tau, prm: Params):
 
     Wgas = V
     Wbme = {d: ustar[d][d] for d in DIRS}
+    if prm.flux == "B":
+        Wgas, Wbme = _diagonal_mean(Wgas), _diagonal_mean(Wbme)
+    elif prm.flux != "A":
+        raise ValueError(prm.flux)
     new = {k: transport(gas1[k], Wgas) for k in GAS_FIELDS}
     new.update({k: transport(bme1[k], Wbme) for k in BME_FIELDS})
 
@@ -333,6 +341,20 @@ def advance(st, phi, tau, prm: Params):
         nEk = np.where(take, new["nE" + k], new["P" + k] + qq[k])
         new["P" + k], new["nE" + k] = Pk, nEk
     return new, {"kappa_gas": kap_gas, "kappa_bme": kap_bme}
+
+
+def _diagonal_mean(W):
+    """Reading B of s1: the axis-d face velocity averaged over the four transverse
+    diagonal neighbours of the face, (k +- 1, l +- 1) in the two tangent directions."""
+    out = {}
+    for d in DIRS:
+        t1, t2 = _TANGENTS[d]
+        acc = 0.0
+        for a in (-1, 1):
+            for b in (-1, 1):
+                acc = acc + np.roll(np.roll(W[d], a, axis=_AXIS[t1]), b, axis=_AXIS[t2])
+        out[d] = 0.25 * acc
+    return out
 
 
 def _wrap_take(a, idx, axis):
