@@ -78,8 +78,76 @@ template <typename C, bool INV> struct Butterfly<C, INV, 3> {
     }
 };
 
+// 8- and 16-point DFTs as two layers of 4-point DFTs (and a 2-point layer for
+// 8): with n = 4 n1 + n2 (n = 2 n1 + n2 for 8) and k = k1 + 4 k2,
+//   X[k1 + 4 k2] = sum_n2 W4^(n2 k2) [ W_R^(n2 k1) sum_n1 x[n] W4^(n1 k1) ],
+// W_R = exp(-2 pi i / R) (conjugate for the inverse).
+template <typename C, bool INV>
+__device__ __forceinline__ C rot(C v, double c, double s) {   // v * (c - i s) forward, (c + i s) inverse
+    typedef decltype(C().x) R;
+    const R cr = R(c), sr = INV ? R(-s) : R(s);
+    C r;
+    r.x = v.x * cr + v.y * sr;
+    r.y = v.y * cr - v.x * sr;
+    return r;
+}
+template <typename C, bool INV> struct Butterfly<C, INV, 8> {
+    static __device__ __forceinline__ void run(C* x) {
+        constexpr double h = 0.70710678118654752440;   // cos(pi/4) = sin(pi/4)
+        C z[2][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) {
+            C t[4] = {x[n2], x[2 + n2], x[4 + n2], x[6 + n2]};
+            Butterfly<C, INV, 4>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) z[n2][k1] = t[k1];
+        }
+        // W8^(k1) for n2 = 1: k1 = 1: (h, h); 2: (0, 1); 3: (-h, h) as (cos, sin)
+        z[1][1] = rot<C, INV>(z[1][1], h, h);
+        z[1][2] = rot<C, INV>(z[1][2], 0.0, 1.0);
+        z[1][3] = rot<C, INV>(z[1][3], -h, h);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            x[k1] = cadd(z[0][k1], z[1][k1]);
+            x[k1 + 4] = csub(z[0][k1], z[1][k1]);
+        }
+    }
+};
+template <typename C, bool INV> struct Butterfly<C, INV, 16> {
+    static __device__ __forceinline__ void run(C* x) {
+        // cos and sin of 2 pi m / 16, m = 0..9
+        constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173;
+        constexpr double h = 0.70710678118654752440;
+        const double cs[10][2] = {{1.0, 0.0}, {c1, s1}, {h, h}, {s1, c1}, {0.0, 1.0},
+                                  {-s1, c1}, {-h, h}, {-c1, s1}, {-1.0, 0.0}, {-c1, -s1}};
+        C z[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            C t[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
+            Butterfly<C, INV, 4>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) {
+                const int m = n2 * k1;   // twiddle W16^(n2 k1), 0 <= m <= 9
+                z[n2][k1] = (m == 0) ? t[k1] : rot<C, INV>(t[k1], cs[m][0], cs[m][1]);
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C t[4] = {z[0][k1], z[1][k1], z[2][k1], z[3][k1]};
+            Butterfly<C, INV, 4>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = t[k2];
+        }
+    }
+};
+
 template <int L> struct FirstRadix {
     static constexpr int value = (L % 4 == 0) ? 4 : (L % 2 == 0) ? 2 : (L % 3 == 0) ? 3 : 1;
+};
+// Radix sequence of the in-place column passes: 16 first (fewest passes
+// through shared memory), then 8, 4, 2, 3.
+template <int L> struct RadixIP {
+    static constexpr int value = (L % 16 == 0) ? 16 : (L % 8 == 0) ? 8 : FirstRadix<L>::value;
 };
 
 // One Stockham pass of radix R at span NS over NL lines of length L held in
@@ -176,7 +244,7 @@ __device__ __forceinline__ void stockham_pass_ip(C* A, const C* tw) {
 template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int REM, int TWL, int NTHR>
 struct StockhamIP {
     static __device__ __forceinline__ void run(C* A, const C* tw) {
-        constexpr int R = FirstRadix<REM>::value;
+        constexpr int R = RadixIP<REM>::value;
         static_assert(R > 1, "transform length must be 2^a 3^b");
         stockham_pass_ip<C, INV, L, NL, SJ, SL, LFAST, NS, R, TWL, NTHR>(A, tw);
         StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS * R, REM / R, TWL, NTHR>::run(A, tw);
