@@ -54,12 +54,12 @@ static cudaError_t solve_n(const T* rho, const T* nd, T* phi, void* spec_v, cons
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
     // total scale of the unnormalised inverse: 1 / ((N/2) N N)
     const double coef = -4.0 * 3.14159265358979323846 * coef_G_h2 / (double(Gm::M) * N * N);
-    fft_x_forward<T, N, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
+    fft_x_forward<T, N, N><<<dim3(gx, nb), Gm::NTX, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
     fft_y<T, N, N, false><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, bs_spec);
     fft_z_solve<T, N, N, false><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, asin2, T(coef), nullptr,
                                                                           bs_spec);
     fft_y<T, N, N, true><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, bs_spec);
-    fft_x_inverse<T, N, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
+    fft_x_inverse<T, N, N><<<dim3(gx, nb), Gm::NTX, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
     return cudaGetLastError();
 }
 

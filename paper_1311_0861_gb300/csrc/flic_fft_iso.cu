@@ -94,7 +94,7 @@ static cudaError_t green_init_n(double h, double G, T* gtab, T* greal, void* tmp
     const int nrows = L * L;
     const int gx = (nrows + Gm::RB - 1) / Gm::RB;
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
-    fft_x_forward<T, L, L><<<gx, 256, Gm::smem_x, st>>>(greal, nullptr, spec, nrows, tw, 0, 0);
+    fft_x_forward<T, L, L><<<gx, Gm::NTX, Gm::smem_x, st>>>(greal, nullptr, spec, nrows, tw, 0, 0);
     fft_y<T, L, L, false><<<dim3(gk, L), Gm::NTC, Gm::smem_c, st>>>(spec, tw, 0);
     const double scale = 1.0 / (double(L / 2) * L * L);
     fft_z_green<T, L><<<dim3(gk, L / 2 + 1), Gm::NTC, Gm::smem_c, st>>>(spec, tw, T(scale), gtab);
@@ -112,11 +112,11 @@ static cudaError_t solve_iso_n(const T* rho, const T* nd, T* phi, void* spec_v, 
     const int nrows = N * N;
     const int gx = (nrows + Gm::RB - 1) / Gm::RB;
     const int gk = (Gm::MH + Gm::KB - 1) / Gm::KB;
-    fft_x_forward<T, L, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
+    fft_x_forward<T, L, N><<<dim3(gx, nb), Gm::NTX, Gm::smem_x, st>>>(rho, nd, spec, nrows, tw, bs_in, bs_spec);
     fft_y<T, L, N, false><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, bs_spec);
     fft_z_solve<T, L, N, true><<<dim3(gk, L, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, nullptr, T(0), gtab, bs_spec);
     fft_y<T, L, N, true><<<dim3(gk, N, nb), Gm::NTC, Gm::smem_c, st>>>(spec, tw, bs_spec);
-    fft_x_inverse<T, L, N><<<dim3(gx, nb), 256, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
+    fft_x_inverse<T, L, N><<<dim3(gx, nb), Gm::NTX, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
     return cudaGetLastError();
 }
 

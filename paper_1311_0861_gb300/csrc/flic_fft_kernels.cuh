@@ -255,21 +255,23 @@ struct StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL, NTHR> {
     static __device__ __forceinline__ void run(C*, const C*) {}
 };
 
-// Block sizes: rows per block of the x passes (~16 KB of complex data per
-// buffer, two buffers, 256 threads); columns per block of the y/z passes: KB
+// Block sizes: rows per block of the x passes (at least 8, at least 1024
+// elements; one in-place buffer, NTX threads of 16 elements each); columns per block of the y/z passes: KB
 // columns (up to 16, i.e. 128-byte row segments in float32) of length L in one
 // in-place buffer of at most 64 KB (three blocks per SM), NTC threads (16
 // elements each).
 template <typename T, int L> struct FftGeom {
     typedef typename C2<T>::t C;
     static constexpr int M = L / 2, MH = M + 1;
-    static constexpr int RB0 = int(16384 / (sizeof(C) * M));
-    static constexpr int RB = RB0 < 1 ? 1 : (RB0 > 64 ? 64 : RB0);
+    static constexpr int RB0 = 1024 / M;   // 8 rows from M = 128 up (measured best at M = 128 and 512)
+    static constexpr int RB = RB0 < 8 ? 8 : (RB0 > 64 ? 64 : RB0);
+    static constexpr int NTX0 = (RB * M / 16 + 31) / 32 * 32;
+    static constexpr int NTX = NTX0 < 32 ? 32 : (NTX0 > 1024 ? 1024 : NTX0);
     static constexpr int KLIM = int(65536 / (sizeof(C) * L));
     static constexpr int KB = KLIM >= 16 ? 16 : KLIM >= 8 ? 8 : KLIM >= 4 ? 4 : KLIM >= 2 ? 2 : 1;
     static constexpr int NTC0 = (L * KB / 16 + 31) / 32 * 32;
     static constexpr int NTC = NTC0 < 64 ? 64 : (NTC0 > 1024 ? 1024 : NTC0);
-    static constexpr size_t smem_x = (size_t(2) * RB * M + L) * sizeof(C);
+    static constexpr size_t smem_x = (size_t(RB) * M + L) * sizeof(C);
     static constexpr size_t smem_c = (size_t(L) * KB + L) * sizeof(C);
 };
 
@@ -284,13 +286,13 @@ __device__ __forceinline__ void stage_twiddles(C* tws, const C* __restrict__ tw)
 // L/2 + 1 modes.
 // ---------------------------------------------------------------------------
 template <typename T, int L, int P>
-__global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, const T* __restrict__ b,
-                                                     typename C2<T>::t* __restrict__ spec, int nrows,
-                                                     const typename C2<T>::t* __restrict__ tw, size_t bs_in,
-                                                     size_t bs_spec) {
+__global__ void __launch_bounds__(FftGeom<T, L>::NTX) fft_x_forward(const T* __restrict__ a, const T* __restrict__ b,
+                                                                    typename C2<T>::t* __restrict__ spec, int nrows,
+                                                                    const typename C2<T>::t* __restrict__ tw,
+                                                                    size_t bs_in, size_t bs_spec) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
-    constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB;
+    constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB, NTX = Gm::NTX;
     static_assert(P % 2 == 0 && P <= L, "physical extent");
     // batch of independent runs along grid y
     a += blockIdx.y * bs_in;
@@ -298,11 +300,12 @@ __global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, co
     spec += blockIdx.y * bs_spec;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
-    C* B = A + RB * M;
-    C* tws = B + RB * M;
+    C* tws = A + RB * M;
     stage_twiddles<C, L>(tws, tw);
     const int row0 = blockIdx.x * RB;
-    for (int t = threadIdx.x; t < RB * M; t += blockDim.x) {
+    // pairs of reals load as one complex (row starts and P are even)
+#pragma unroll 4
+    for (int t = threadIdx.x; t < RB * M; t += NTX) {
         const int l = t / M, j = t % M;
         const int row = row0 + l;
         C z;
@@ -310,18 +313,19 @@ __global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, co
         z.y = T(0);
         if (row < nrows && 2 * j < P) {
             const size_t g = size_t(row) * P + 2 * j;
-            z.x = a[g];
-            z.y = a[g + 1];
+            z = *reinterpret_cast<const C*>(a + g);
             if (b) {
-                z.x += b[g];
-                z.y += b[g + 1];
+                const C w = *reinterpret_cast<const C*>(b + g);
+                z.x += w.x;
+                z.y += w.y;
             }
         }
         A[l * M + j] = z;
     }
     __syncthreads();
-    C* Z = Stockham<C, false, M, RB, 1, M, false, 1, M, L>::run(A, B, tws);
-    for (int t = threadIdx.x; t < RB * MH; t += blockDim.x) {
+    StockhamIP<C, false, M, RB, 1, M, false, 1, M, L, NTX>::run(A, tws);
+    const C* Z = A;
+    for (int t = threadIdx.x; t < RB * MH; t += NTX) {
         const int l = t / MH, k = t % MH;
         const int row = row0 + l;
         if (row >= nrows) continue;
@@ -341,23 +345,22 @@ __global__ void __launch_bounds__(256) fft_x_forward(const T* __restrict__ a, co
 // X pass, inverse: L/2 + 1 modes per physical row -> the first P reals
 // ---------------------------------------------------------------------------
 template <typename T, int L, int P>
-__global__ void __launch_bounds__(256) fft_x_inverse(const typename C2<T>::t* __restrict__ spec,
-                                                     T* __restrict__ phi, int nrows,
-                                                     const typename C2<T>::t* __restrict__ tw, size_t bs_spec,
-                                                     size_t bs_phi) {
+__global__ void __launch_bounds__(FftGeom<T, L>::NTX) fft_x_inverse(const typename C2<T>::t* __restrict__ spec,
+                                                                    T* __restrict__ phi, int nrows,
+                                                                    const typename C2<T>::t* __restrict__ tw,
+                                                                    size_t bs_spec, size_t bs_phi) {
     typedef typename C2<T>::t C;
     typedef FftGeom<T, L> Gm;
-    constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB;
+    constexpr int M = Gm::M, MH = Gm::MH, RB = Gm::RB, NTX = Gm::NTX;
     spec += blockIdx.y * bs_spec;
     phi += blockIdx.y * bs_phi;
     extern __shared__ __align__(16) unsigned char sm[];
     C* A = reinterpret_cast<C*>(sm);
-    C* B = A + RB * M;
-    C* tws = B + RB * M;
+    C* tws = A + RB * M;
     stage_twiddles<C, L>(tws, tw);
     __syncthreads();
     const int row0 = blockIdx.x * RB;
-    for (int t = threadIdx.x; t < RB * M; t += blockDim.x) {
+    for (int t = threadIdx.x; t < RB * M; t += NTX) {
         const int l = t / M, k = t % M;
         const int row = row0 + l;
         C z;
@@ -379,15 +382,13 @@ __global__ void __launch_bounds__(256) fft_x_inverse(const typename C2<T>::t* __
         A[l * M + k] = z;
     }
     __syncthreads();
-    C* Z = Stockham<C, true, M, RB, 1, M, false, 1, M, L>::run(A, B, tws);
-    for (int t = threadIdx.x; t < RB * M; t += blockDim.x) {
+    StockhamIP<C, true, M, RB, 1, M, false, 1, M, L, NTX>::run(A, tws);
+    for (int t = threadIdx.x; t < RB * M; t += NTX) {
         const int l = t / M, j = t % M;
         const int row = row0 + l;
         if (row >= nrows || 2 * j >= P) continue;
-        C z = Z[l * M + j];
         const size_t g = size_t(row) * P + 2 * j;
-        phi[g] = z.x;
-        phi[g + 1] = z.y;
+        *reinterpret_cast<C*>(phi + g) = A[l * M + j];   // two reals as one complex
     }
 }
 
