@@ -118,14 +118,17 @@ int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out);
 
 /* Copies 22 host float64 arrays (field order above, N^3 each) to the device,
  * converting to the storage precision on the device, and computes the initial
- * signal speed.  Returns FLIC_ERR_NONPHYSICAL if the state has rho, n, e or
- * Pi_dd <= 0 or a non-finite value (the state is still stored). */
+ * signal speed.  Page-locked, device-mapped arrays (cudaHostAlloc) are read in
+ * place by the conversion kernel; pageable arrays go through a staging copy.
+ * Returns FLIC_ERR_NONPHYSICAL if the state has rho, n, e or Pi_dd <= 0 or a
+ * non-finite value (the state is still stored). */
 int flic_set_state(flic_handle* h, const double* const fields[FLIC_NFIELDS]);
 
 /* Same, from 22 device float64 arrays owned by the caller. */
 int flic_set_state_device(flic_handle* h, const double* const fields[FLIC_NFIELDS]);
 
-/* Copies the state to 22 host float64 arrays (N^3 each). */
+/* Copies the state to 22 host float64 arrays (N^3 each); page-locked mapped
+ * arrays are written in place by the conversion kernel. */
 int flic_get_state(flic_handle* h, double* const fields[FLIC_NFIELDS]);
 
 /* Same, into 22 device float64 arrays owned by the caller. */

@@ -164,9 +164,13 @@ static int set_state_impl(flic_handle* h, const double* const* fields, bool devi
         if (!fields[f]) { h->err = "null field pointer"; return FLIC_ERR_INVALID_ARG; }
         const double* src = fields[f];
         if (!device) {
-            FLIC_CK(h, cudaMemcpyAsync(h->staging, fields[f], h->cells * sizeof(double),
-                                       cudaMemcpyHostToDevice, h->st));
-            src = h->staging;
+            // page-locked host arrays are read in place by the conversion kernel
+            src = static_cast<const double*>(mapped_device_view(fields[f]));
+            if (!src) {
+                FLIC_CK(h, cudaMemcpyAsync(h->staging, fields[f], h->cells * sizeof(double),
+                                           cudaMemcpyHostToDevice, h->st));
+                src = h->staging;
+            }
         }
         FLIC_CK(h, convert_in<T>(src, field_ptr<T>(h->state[h->cur], h->fs, f), h->cells, h->st));
     }
@@ -180,8 +184,10 @@ static int get_state_impl(flic_handle* h, double* const* fields, bool device) {
     for (int f = 0; f < F_COUNT; ++f) {
         if (!fields[f]) { h->err = "null field pointer"; return FLIC_ERR_INVALID_ARG; }
         const T* src = field_ptr<T>(h->state[h->cur], h->fs, f);
-        if (device) {
-            FLIC_CK(h, convert_out<T>(src, fields[f], h->cells, h->st));
+        double* view = device ? fields[f] : static_cast<double*>(const_cast<void*>(mapped_device_view(fields[f])));
+        if (view) {
+            // device arrays, or page-locked host arrays written in place
+            FLIC_CK(h, convert_out<T>(src, view, h->cells, h->st));
         } else {
             FLIC_CK(h, convert_out<T>(src, h->staging, h->cells, h->st));
             FLIC_CK(h, cudaMemcpyAsync(fields[f], h->staging, h->cells * sizeof(double), cudaMemcpyDeviceToHost,

@@ -316,8 +316,12 @@ int ens_set_state(flic_ensemble* e, int r, const double* const* fields) {
     T* base = reinterpret_cast<T*>(c.state[e->cur]) + size_t(e->run_slot[r]) * c.run_stride;
     for (int f = 0; f < F_COUNT; ++f) {
         if (!fields[f]) { e->err = "null field pointer"; return FLIC_ERR_INVALID_ARG; }
-        ENS_CK(e, cudaMemcpyAsync(e->staging, fields[f], cells * sizeof(double), cudaMemcpyHostToDevice, e->st));
-        ENS_CK(e, convert_in<T>(e->staging, base + size_t(f) * c.fs, cells, e->st));
+        const double* src = static_cast<const double*>(mapped_device_view(fields[f]));
+        if (!src) {
+            ENS_CK(e, cudaMemcpyAsync(e->staging, fields[f], cells * sizeof(double), cudaMemcpyHostToDevice, e->st));
+            src = e->staging;
+        }
+        ENS_CK(e, convert_in<T>(src, base + size_t(f) * c.fs, cells, e->st));
     }
     double* sc = e->scal + size_t(r) * S_COUNT;
     ENS_CK(e, cudaMemsetAsync(sc, 0, S_COUNT * sizeof(double), e->st));
@@ -342,8 +346,14 @@ int ens_get_state(flic_ensemble* e, int r, double* const* fields) {
     const T* base = reinterpret_cast<const T*>(c.state[e->cur]) + size_t(e->run_slot[r]) * c.run_stride;
     for (int f = 0; f < F_COUNT; ++f) {
         if (!fields[f]) { e->err = "null field pointer"; return FLIC_ERR_INVALID_ARG; }
-        ENS_CK(e, convert_out<T>(base + size_t(f) * c.fs, e->staging, cells, e->st));
-        ENS_CK(e, cudaMemcpyAsync(fields[f], e->staging, cells * sizeof(double), cudaMemcpyDeviceToHost, e->st));
+        double* view = static_cast<double*>(const_cast<void*>(mapped_device_view(fields[f])));
+        if (view) {
+            ENS_CK(e, convert_out<T>(base + size_t(f) * c.fs, view, cells, e->st));
+        } else {
+            ENS_CK(e, convert_out<T>(base + size_t(f) * c.fs, e->staging, cells, e->st));
+            ENS_CK(e, cudaMemcpyAsync(fields[f], e->staging, cells * sizeof(double), cudaMemcpyDeviceToHost,
+                                      e->st));
+        }
     }
     ENS_CK(e, cudaStreamSynchronize(e->st));
     return FLIC_OK;

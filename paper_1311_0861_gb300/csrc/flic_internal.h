@@ -34,6 +34,7 @@ cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, 
 
 // float64 <-> storage precision conversion of one field.
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);
+const void* mapped_device_view(const void* host_ptr);
 template <typename T> cudaError_t convert_out(const T* src, double* dst, size_t n, cudaStream_t st);
 
 // The 22 field arrays of a state.

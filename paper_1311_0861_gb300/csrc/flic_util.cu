@@ -14,14 +14,86 @@ __global__ void convert_out_kernel(const T* __restrict__ src, double* __restrict
         dst[i] = double(src[i]);
 }
 
+// Pairs of elements per access (16-byte float64 loads or stores), four pairs in
+// flight per thread: the host side of these copies may be page-locked memory
+// read or written across the CPU-GPU link, where bytes in flight set the rate.
+template <typename T> struct Pair;
+template <> struct Pair<float> { typedef float2 t; };
+template <> struct Pair<double> { typedef double2 t; };
+
+template <typename T>
+__global__ void convert_in_pairs(const double2* __restrict__ src, typename Pair<T>::t* __restrict__ dst, size_t npair) {
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+    for (; i + 3 * stride < npair; i += 4 * stride) {
+        double2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = src[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            typename Pair<T>::t w;
+            w.x = T(v[k].x);
+            w.y = T(v[k].y);
+            dst[i + k * stride] = w;
+        }
+    }
+    for (; i < npair; i += stride) {
+        const double2 v = src[i];
+        typename Pair<T>::t w;
+        w.x = T(v.x);
+        w.y = T(v.y);
+        dst[i] = w;
+    }
+}
+template <typename T>
+__global__ void convert_out_pairs(const typename Pair<T>::t* __restrict__ src, double2* __restrict__ dst, size_t npair) {
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+    for (; i + 3 * stride < npair; i += 4 * stride) {
+        typename Pair<T>::t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = src[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[i + k * stride] = make_double2(double(v[k].x), double(v[k].y));
+    }
+    for (; i < npair; i += stride) {
+        const typename Pair<T>::t v = src[i];
+        dst[i] = make_double2(double(v.x), double(v.y));
+    }
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st) {
-    convert_in_kernel<T><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    if (n % 2 == 0 && aligned(src, 16) && aligned(dst, 2 * sizeof(T))) {
+        convert_in_pairs<T><<<152 * 8, 256, 0, st>>>(reinterpret_cast<const double2*>(src),
+                                                      reinterpret_cast<typename Pair<T>::t*>(dst), n / 2);
+    } else {
+        convert_in_kernel<T><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    }
     return cudaGetLastError();
 }
 template <typename T> cudaError_t convert_out(const T* src, double* dst, size_t n, cudaStream_t st) {
-    convert_out_kernel<T><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    if (n % 2 == 0 && aligned(dst, 16) && aligned(src, 2 * sizeof(T))) {
+        convert_out_pairs<T><<<152 * 8, 256, 0, st>>>(reinterpret_cast<const typename Pair<T>::t*>(src),
+                                                       reinterpret_cast<double2*>(dst), n / 2);
+    } else {
+        convert_out_kernel<T><<<152 * 8, 256, 0, st>>>(src, dst, n);
+    }
     return cudaGetLastError();
 }
+// Device address of a host buffer the GPU reads and writes directly (page-locked
+// and mapped into the device address space, e.g. cudaHostAlloc'd), or null for
+// pageable memory, which goes through a staging copy instead.
+const void* mapped_device_view(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
+}
+
 template cudaError_t convert_in<float>(const double*, float*, size_t, cudaStream_t);
 template cudaError_t convert_in<double>(const double*, double*, size_t, cudaStream_t);
 template cudaError_t convert_out<float>(const float*, double*, size_t, cudaStream_t);

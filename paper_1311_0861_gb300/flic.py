@@ -329,11 +329,23 @@ class Ensemble:
             ptrs.append(p)
         self._check(self.lib.flic_ensemble_set_state(self._e, run, (ctypes.c_void_p * NFIELDS)(*ptrs)))
 
-    def get_state(self, run: int) -> dict:
+    def get_state(self, run: int, out=None):
+        """The run's state as a dict of float64 (n, n, n) numpy arrays, or into
+        ``out`` (dict or sequence of 22 host float64 arrays, numpy or torch)."""
         n = self.sizes[run]
-        res = {f: np.empty((n, n, n)) for f in FIELDS}
-        ptrs = (ctypes.c_void_p * NFIELDS)(*[res[f].ctypes.data for f in FIELDS])
-        self._check(self.lib.flic_ensemble_get_state(self._e, run, ptrs))
+        if out is None:
+            res = {f: np.empty((n, n, n)) for f in FIELDS}
+            arrs = [res[f] for f in FIELDS]
+        else:
+            res = out
+            arrs = _field_list(out, n)
+        ptrs = []
+        for a in arrs:
+            p, dev = _ptr_of(a, False)
+            if dev:
+                raise FlicError(ERR_INVALID_ARG, "ensemble states are host arrays")
+            ptrs.append(p)
+        self._check(self.lib.flic_ensemble_get_state(self._e, run, (ctypes.c_void_p * NFIELDS)(*ptrs)))
         return res
 
     def step(self, nsteps: int = 1, dt: float = 0.0, sync: bool = True):

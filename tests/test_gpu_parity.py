@@ -279,3 +279,30 @@ def test_outflow_ten_steps_fp64_graph(flic):
         out = g.get_state()
     err = rel_l1(out, ref)
     assert max(err.values()) <= 1e-10, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pinned_host_state_round_trip(flic, precision):
+    """Page-locked host arrays (read and written in place by the conversion
+    kernels) give the same state as pageable ones."""
+    torch = pytest.importorskip("torch")
+    s = I.random_state((24, 24, 24), seed=6, rough=True)
+    pinned_in = torch.empty((22, 24, 24, 24), dtype=torch.float64, pin_memory=True)
+    pinned_out = torch.empty((22, 24, 24, 24), dtype=torch.float64, pin_memory=True)
+    pinned_in.numpy()[...] = I.stack(s.state)
+    with flic.Grid(24, precision=precision, box=(-1.0, -1.0 + 24 * s.h)) as g:
+        g.set_state([pinned_in[i] for i in range(22)])
+        ref = g.get_state()
+        g.get_state([pinned_out[i] for i in range(22)])
+        g.step()
+        a = g.get_state()
+        g.set_state(s.state)
+        g.step()
+        b = g.get_state()
+    got = I.unstack(pinned_out.numpy())
+    for f in FIELDS:
+        assert np.array_equal(got[f], ref[f]), f
+        assert np.array_equal(a[f], b[f]), f
+    if precision == "fp64":
+        for f in FIELDS:
+            assert np.array_equal(ref[f], s.state[f]), f
