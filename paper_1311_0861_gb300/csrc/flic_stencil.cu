@@ -9,12 +9,13 @@ template <typename T> struct Tiles;
 // Launch shapes (TileCfg: tile, min blocks per SM, staged energy tensor, one
 // thread per updated cell, helper face rounds), chosen by measurement at 256^3.
 // float32 gas: 32 x 8, one thread per tile cell, three blocks per SM.
-// float32 moments: 32 x 12 with 480 threads (384 tile + 96 helpers), one block
-// per SM and no register cap -- faster than 256-thread blocks two per SM, whose
-// 128-register cap spills and whose border cells take a second phase-1 round.
+// float32 moments: 32 x 12 with 480 threads (384 tile + 96 helpers taking 5 faces
+// each first), one block per SM and no register cap -- faster than 256-thread
+// blocks two per SM, whose 128-register cap spills and whose border cells take
+// a second phase-1 round (helper rounds 5 / 6 / 7: 1.153 / 1.164 / 1.175 ms).
 template <> struct Tiles<float> {
     using Gas = TileCfg<32, 8, 3, false, false, 0>;
-    using Bme = TileCfg<32, 12, 1, false, true, 6>;
+    using Bme = TileCfg<32, 12, 1, false, true, 5>;
 };
 template <> struct Tiles<double> {
     using Gas = TileCfg<32, 8, 2, false, false, 0>;
