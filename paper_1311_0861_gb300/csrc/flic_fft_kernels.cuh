@@ -199,12 +199,18 @@ struct Stockham<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL> {
 // reads the inputs of its butterflies into registers, the block synchronises,
 // then the outputs overwrite the same buffer (one buffer instead of two, so
 // twice the lines fit in shared memory).
-template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int R, int TWL, int NTHR>
+// HALF bit 0: the line's second half is zero (zero-padded input), so the first
+// pass (span 1) skips loading it; bit 1: only the first half of the result is
+// wanted, so the last pass (span L/R) stores only its first R/2 outputs.
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int R, int TWL, int NTHR,
+          int HALF = 0>
 __device__ __forceinline__ void stockham_pass_ip(C* A, const C* tw) {
     constexpr int NB = L / R;
     constexpr int TOTAL = NB * NL;
     constexpr int PER = (TOTAL + NTHR - 1) / NTHR;
     constexpr int TSC = (TWL / L) * (L / (NS * R));
+    constexpr bool ZIN = (HALF & 1) && NS == 1 && R % 2 == 0;
+    constexpr bool HOUT = (HALF & 2) && NS * R == L && R % 2 == 0;
     C x[PER][R];
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
@@ -213,7 +219,14 @@ __device__ __forceinline__ void stockham_pass_ip(C* A, const C* tw) {
             const int l = LFAST ? t % NL : t / NB;
             const int j = LFAST ? t / NL : t % NB;
 #pragma unroll
-            for (int q = 0; q < R; ++q) x[p][q] = A[(j + q * NB) * SJ + l * SL];
+            for (int q = 0; q < R; ++q) {
+                if (ZIN && q >= R / 2) {   // index j + q L/R >= L/2
+                    x[p][q].x = 0;
+                    x[p][q].y = 0;
+                } else {
+                    x[p][q] = A[(j + q * NB) * SJ + l * SL];
+                }
+            }
         }
     }
     __syncthreads();
@@ -235,23 +248,24 @@ __device__ __forceinline__ void stockham_pass_ip(C* A, const C* tw) {
             Butterfly<C, INV, R>::run(x[p]);
             const int idx = (j / NS) * NS * R + k;
 #pragma unroll
-            for (int q = 0; q < R; ++q) A[(idx + q * NS) * SJ + l * SL] = x[p][q];
+            for (int q = 0; q < (HOUT ? R / 2 : R); ++q) A[(idx + q * NS) * SJ + l * SL] = x[p][q];
         }
     }
     __syncthreads();
 }
 
-template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int REM, int TWL, int NTHR>
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int REM, int TWL, int NTHR,
+          int HALF = 0>
 struct StockhamIP {
     static __device__ __forceinline__ void run(C* A, const C* tw) {
         constexpr int R = RadixIP<REM>::value;
         static_assert(R > 1, "transform length must be 2^a 3^b");
-        stockham_pass_ip<C, INV, L, NL, SJ, SL, LFAST, NS, R, TWL, NTHR>(A, tw);
-        StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS * R, REM / R, TWL, NTHR>::run(A, tw);
+        stockham_pass_ip<C, INV, L, NL, SJ, SL, LFAST, NS, R, TWL, NTHR, HALF>(A, tw);
+        StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS * R, REM / R, TWL, NTHR, HALF>::run(A, tw);
     }
 };
-template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int TWL, int NTHR>
-struct StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL, NTHR> {
+template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int TWL, int NTHR, int HALF>
+struct StockhamIP<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL, NTHR, HALF> {
     static __device__ __forceinline__ void run(C*, const C*) {}
 };
 
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTX) fft_x_forward(const T* __r
         A[l * M + j] = z;
     }
     __syncthreads();
-    StockhamIP<C, false, M, RB, 1, M, false, 1, M, L, NTX>::run(A, tws);
+    StockhamIP<C, false, M, RB, 1, M, false, 1, M, L, NTX, (2 * P <= L) ? 1 : 0>::run(A, tws);
     const C* Z = A;
     for (int t = threadIdx.x; t < RB * MH; t += NTX) {
         const int l = t / MH, k = t % MH;
@@ -382,7 +396,7 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTX) fft_x_inverse(const typena
         A[l * M + k] = z;
     }
     __syncthreads();
-    StockhamIP<C, true, M, RB, 1, M, false, 1, M, L, NTX>::run(A, tws);
+    StockhamIP<C, true, M, RB, 1, M, false, 1, M, L, NTX, (2 * P <= L) ? 2 : 0>::run(A, tws);
     for (int t = threadIdx.x; t < RB * M; t += NTX) {
         const int l = t / M, j = t % M;
         const int row = row0 + l;
@@ -420,7 +434,9 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_y(typename C2<T>::t* _
         A[y * KB + c] = v;
     }
     __syncthreads();
-    StockhamIP<C, INV, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
+    // forward: the rows beyond NIN are zero; inverse: only the first NOUT rows are kept
+    StockhamIP<C, INV, L, KB, KB, 1, true, 1, L, L, NTC,
+               (!INV && 2 * NIN <= L) ? 1 : ((INV && 2 * NOUT <= L) ? 2 : 0)>::run(A, tws);
     for (int t = threadIdx.x; t < NOUT * KB; t += NTC) {
         const int c = t % KB, y = t / KB;
         if (k0 + c < MH) spec[base + size_t(y) * MH + k0 + c] = A[y * KB + c];
@@ -460,7 +476,7 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_solve(typename C2<T>
         A[z * KB + c] = v;
     }
     __syncthreads();
-    StockhamIP<C, false, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
+    StockhamIP<C, false, L, KB, KB, 1, true, 1, L, L, NTC, (2 * P <= L) ? 1 : 0>::run(A, tws);
     const int ys = y <= L / 2 ? y : L - y;
     for (int t = threadIdx.x; t < L * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
@@ -483,7 +499,7 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_solve(typename C2<T>
         A[z * KB + c] = v;   // each element is read and written by the same thread
     }
     __syncthreads();
-    StockhamIP<C, true, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
+    StockhamIP<C, true, L, KB, KB, 1, true, 1, L, L, NTC, (2 * P <= L) ? 2 : 0>::run(A, tws);
     for (int t = threadIdx.x; t < P * KB; t += NTC) {
         const int c = t % KB, z = t / KB;
         if (k0 + c < MH) spec[base + size_t(z) * zs + k0 + c] = A[z * KB + c];
