@@ -26,7 +26,7 @@ struct flic_handle {
     void* tw = nullptr;
     int tw_len = 0;
     void* asin2 = nullptr;
-    void* gtab = nullptr;             // isolated mode: scaled transform of the Green's function, (N+1)^3
+    void* gtab = nullptr;             // isolated mode: scaled transform of the Green's function, ~(N+1)^3
     bool iso = false;
     FftPlans plans;
     double* scal = nullptr;
@@ -258,7 +258,7 @@ static int init_impl(flic_handle* h) {
     }
     if (h->iso) {
         // transform of the Green's function, computed once with temporary workspace
-        FLIC_CK(h, cudaMalloc(&h->gtab, size_t(N + 1) * (N + 1) * (N + 1) * sizeof(T)));
+        FLIC_CK(h, cudaMalloc(&h->gtab, green_table_elems<T>(N) * sizeof(T)));
         void* greal = nullptr;
         void* gspec = nullptr;
         cudaError_t e = cudaMalloc(&greal, size_t(L) * L * L * sizeof(T));

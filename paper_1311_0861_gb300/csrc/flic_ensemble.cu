@@ -201,7 +201,7 @@ int ens_init(flic_ensemble* e) {
         ENS_CK(e, cudaMalloc(&c.asin2, N * sizeof(T)));
         ENS_CK(e, cudaMemcpy(c.asin2, a2.data(), N * sizeof(T), cudaMemcpyHostToDevice));
         if (e->iso) {
-            ENS_CK(e, cudaMalloc(&c.gtab, size_t(N + 1) * (N + 1) * (N + 1) * sizeof(T)));
+            ENS_CK(e, cudaMalloc(&c.gtab, green_table_elems<T>(N) * sizeof(T)));
             void* greal = nullptr;
             void* gspec = nullptr;
             cudaError_t er = cudaMalloc(&greal, size_t(L) * L * L * sizeof(T));

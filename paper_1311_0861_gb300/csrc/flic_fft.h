@@ -38,7 +38,10 @@ cudaError_t poisson_periodic(const T* rho, const T* nd, T* phi, void* spec, int 
                              cudaStream_t st, int nbatch = 1, size_t bs_in = 0, size_t bs_phi = 0,
                              size_t bs_spec = 0);
 
-// Isolated (zero-padded, L = 2N) solve.  gtab: (N+1)^3 reals (the scaled
+// Elements of the isolated solve's Green's function table (about (N+1)^3).
+template <typename T> size_t green_table_elems(int N);
+
+// Isolated (zero-padded, L = 2N) solve.  gtab: green_table_elems reals (the scaled
 // transform of the Green's function, from green_init); spec: N * 2N * (N+1)
 // complex workspace; tw: table of length 2N.  green_init needs (2N)^3 reals
 // (greal) and (2N)^2 (N+1) complex (tmp_spec) of temporary workspace.

@@ -59,10 +59,10 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_green(const typename
     }
     __syncthreads();
     StockhamIP<C, false, L, KB, KB, 1, true, 1, L, L, NTC>::run(A, tws);
-    for (int t = threadIdx.x; t < (L / 2 + 1) * KB; t += NTC) {
-        const int c = t % KB, z = t / KB;
-        if (k0 + c < MH) gtab[(size_t(z) * (L / 2 + 1) + y) * MH + k0 + c] = A[z * KB + c].x * scale;
-    }
+    // layout of the solve's reads: [ky'][kx block][kz'][kx within the block]
+    constexpr int NKB = (MH + KB - 1) / KB;
+    T* out = gtab + (size_t(y) * NKB + blockIdx.x) * (L / 2 + 1) * KB;
+    for (int t = threadIdx.x; t < (L / 2 + 1) * KB; t += NTC) out[t] = A[t].x * scale;   // t = z * KB + c
 }
 
 template <typename T, int N>
@@ -119,6 +119,25 @@ static cudaError_t solve_iso_n(const T* rho, const T* nd, T* phi, void* spec_v, 
     fft_x_inverse<T, L, N><<<dim3(gx, nb), Gm::NTX, Gm::smem_x, st>>>(spec, phi, nrows, tw, bs_spec, bs_phi);
     return cudaGetLastError();
 }
+
+template <typename T, int N>
+static size_t green_elems_n() {
+    typedef FftGeom<T, 2 * N> Gm;
+    constexpr size_t NKB = (Gm::MH + Gm::KB - 1) / Gm::KB;
+    return size_t(N + 1) * (N + 1) * NKB * Gm::KB;
+}
+
+template <typename T>
+size_t green_table_elems(int N) {
+    switch (N) {
+#define FLIC_CASE(n) case n: return green_elems_n<T, n>();
+        FLIC_ISO_SIZES(FLIC_CASE)
+#undef FLIC_CASE
+        default: return 0;
+    }
+}
+template size_t green_table_elems<float>(int);
+template size_t green_table_elems<double>(int);
 
 int fft_iso_supported(int N) {
     switch (N) {

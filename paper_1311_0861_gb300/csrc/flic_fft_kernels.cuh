@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_y(typename C2<T>::t* _
 // inverse (P outputs).  ISO = false: the 27-point symbol of Sec. 2.3 with
 // asin2[k] = 2/3 sin^2(pi k / L) and coef = -4 pi G h^2 * scale; ISO = true:
 // the precomputed transform of the isolated Green's function, stored by its
-// even symmetry as gtab[kz'][ky'][kx], kz' = min(kz, L - kz), ky' likewise.
+// even symmetry for ky' = min(ky, L - ky), kz' likewise, in the order these
+// blocks read it: gtab[ky'][kx block][kz'][kx within the block] (KB columns per
+// block, kx padded to whole blocks), so a block reads one contiguous run.
 // ---------------------------------------------------------------------------
 template <typename T, int L, int P, bool ISO>
 __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_solve(typename C2<T>::t* __restrict__ spec,
@@ -486,7 +488,8 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTC) fft_z_solve(typename C2<T>
             T g;
             if (ISO) {
                 const int zz = z <= L / 2 ? z : L - z;
-                g = gtab[(size_t(zz) * (L / 2 + 1) + ys) * MH + kx];
+                constexpr int NKB = (MH + KB - 1) / KB;
+                g = gtab[((size_t(ys) * NKB + blockIdx.x) * (L / 2 + 1) + zz) * KB + c];
             } else {
                 const T ax = asin2[kx], ay = asin2[y], az = asin2[z];
                 // 1 - f_x f_y f_z without cancellation, f = 1 - a
