@@ -465,6 +465,15 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     constexpr bool SEX = C::SEX;
     constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, H2 = Gm::H2, R1 = Gm::R1, W1 = Gm::W1;
     constexpr int NTH = Gm::NTH, NU = Gm::NU;
+    // float32: the transport runs on field pairs with packed arithmetic (PK);
+    // the gas kernel also stores f' as field pairs (float2 per pair of fields,
+    // pair-major), loaded and stored 8 bytes at a time (FP2).  In the moment
+    // kernel the pair layout measured slower (its loads raise register
+    // pressure past the 128-register budget), so it keeps scalar rows.
+    constexpr bool PK = std::is_same<T, float>::value && P::NF % 2 == 0;
+    constexpr bool FP2 = PK && P::NF < 16;
+    static_assert(!FP2 || (Gm::ring_elems + Gm::xf_elems + Gm::yf_elems + Gm::zc_elems) % 2 == 0,
+                  "the f' buffer must start on an 8-byte boundary");
     constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE, NEX = P::NEX;
     constexpr int NXF = Gm::H1 * Gm::XFW;
     constexpr int NYF = Gm::YFH * W1;
@@ -728,7 +737,15 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                     T f1[NF];
                     P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
+                    if constexpr (FP2) {
+                        // field pairs side by side: one 8-byte store per pair
+#pragma unroll
+                        for (int f = 0; f < NF; f += 2)
+                            reinterpret_cast<float2*>(fpb)[(f / 2) * R1 + c1] = make_float2(f1[f], f1[f + 1]);
+                    } else {
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
+                    }
                     if (i < NT) {
                         // own tile cell (i == tid): keep its face normal velocities for phase 2
                         // (gas: V first on every axis; moments: u*_d is value d)
@@ -756,7 +773,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
             const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
             T out[NF];
-            if constexpr (std::is_same<T, float>::value && NF % 2 == 0) {
+            if constexpr (PK) {
                 // fields in pairs with packed float32 arithmetic (one instruction
                 // for two fields); the same operations as the scalar form below
                 const float2 wz = make_float2(Wzm, Wzm), nr = make_float2(-rat, -rat), pr = make_float2(rat, rat);
@@ -765,11 +782,23 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 const bool zup = Wzm > T(0);
 #pragma unroll
                 for (int f = 0; f < NF; f += 2) {
-                    const T* F0 = fpb + f * R1;
-                    const T* F1 = F0 + R1;
-                    const float2 fc = make_float2(F0[own_c1], F1[own_c1]);
-                    const float2 uxm = make_float2(F0[cxm], F1[cxm]), uxp = make_float2(F0[cxp], F1[cxp]);
-                    const float2 uym = make_float2(F0[cym], F1[cym]), uyp = make_float2(F0[cyp], F1[cyp]);
+                    float2 fc, uxm, uxp, uym, uyp;
+                    if constexpr (FP2) {
+                        const float2* F2 = reinterpret_cast<const float2*>(fpb) + (f / 2) * R1;
+                        fc = F2[own_c1];
+                        uxm = F2[cxm];
+                        uxp = F2[cxp];
+                        uym = F2[cym];
+                        uyp = F2[cyp];
+                    } else {
+                        const T* F0 = fpb + f * R1;
+                        const T* F1 = F0 + R1;
+                        fc = make_float2(F0[own_c1], F1[own_c1]);
+                        uxm = make_float2(F0[cxm], F1[cxm]);
+                        uxp = make_float2(F0[cxp], F1[cxp]);
+                        uym = make_float2(F0[cym], F1[cym]);
+                        uyp = make_float2(F0[cyp], F1[cyp]);
+                    }
                     const float2 Fzm = __fmul2_rn(wz, zup ? make_float2(fprev[f], fprev[f + 1]) : fc);
                     const float2 o = __ffma2_rn(nr, Fzm, make_float2(acc[f], acc[f + 1]));   // completes plane e-1
                     float2 t = __fadd2_rn(__ffma2_rn(nwxm, uxm, __fmul2_rn(wxp, uxp)),
