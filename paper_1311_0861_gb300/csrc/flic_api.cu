@@ -114,6 +114,7 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
     a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, F_RHO);
     a.tz = h->gcfg.tz;
     a.tiles_x = h->gcfg.tiles_x;
+    a.tiles_y = h->gcfg.tiles_y;
     a.partials = h->part_gas;
     FLIC_CK(h, launch_gas<T>(a, h->gcfg, h->st));
     if (ev) FLIC_CK(h, cudaEventRecord(ev[2], h->st));
@@ -122,6 +123,7 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
     a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, F_N);
     a.tz = h->bcfg.tz;
     a.tiles_x = h->bcfg.tiles_x;
+    a.tiles_y = h->bcfg.tiles_y;
     a.partials = h->part_bme;
     FLIC_CK(h, launch_bme<T>(a, h->bcfg, h->st));
     if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));

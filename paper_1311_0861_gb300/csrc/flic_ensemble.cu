@@ -285,11 +285,13 @@ int ens_init(flic_ensemble* e) {
             g.out = out + F_RHO * c.fs;
             g.tz = c.gcfg.tz;
             g.tiles_x = c.gcfg.tiles_x;
+            g.tiles_y = c.gcfg.tiles_y;
             g.partials = e->part_gas + size_t(goff[r]) * Q_COUNT;
             b.in = in + F_N * c.fs;
             b.out = out + F_N * c.fs;
             b.tz = c.bcfg.tz;
             b.tiles_x = c.bcfg.tiles_x;
+            b.tiles_y = c.bcfg.tiles_y;
             b.partials = e->part_bme + size_t(boff[r]) * Q_COUNT;
             tg[p][r] = g;
             tb[p][r] = b;

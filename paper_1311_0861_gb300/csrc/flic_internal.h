@@ -13,10 +13,11 @@ namespace flic {
 struct StepCfg {
     int tx, ty;        // tile shape
     int tiles_x, tiles_y;
-    int tz, blocks_z;
+    int tz, blocks_z;     // tz = 0: balanced split over `balanced` blocks
+    int balanced = 0;
     int threads;
     size_t smem;
-    int num_blocks() const { return tiles_x * tiles_y * blocks_z; }
+    int num_blocks() const { return balanced > 0 ? balanced : tiles_x * tiles_y * blocks_z; }
 };
 
 template <typename T> cudaError_t stencil_prepare();   // shared-memory limits, once

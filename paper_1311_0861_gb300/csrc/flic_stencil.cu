@@ -12,19 +12,25 @@ template <typename T> struct Tiles;
 // float32 moments: 32 x 12 with 480 threads (384 tile + 96 helpers taking 5 faces
 // each first), one block per SM and no register cap -- faster than 256-thread
 // blocks two per SM, whose 128-register cap spills and whose border cells take
-// a second phase-1 round (helper rounds 5 / 6 / 7: 1.153 / 1.164 / 1.175 ms).
+// a second phase-1 round (helper rounds 5 / 6 / 7: 1.153 / 1.164 / 1.175 ms);
+// the balanced split over its 152 resident blocks beats the chunked grid
+// (1.099 vs 1.154 ms), while the gas kernel keeps the chunked grid (0.473 vs
+// 0.492 ms balanced: its neighbouring tiles then share halos in L2).
 template <> struct Tiles<float> {
     using Gas = TileCfg<32, 8, 3, false, false, 0>;
-    using Bme = TileCfg<32, 12, 1, false, true, 5>;
+    using Bme = TileCfg<32, 12, 1, false, true, 5, true>;
 };
 template <> struct Tiles<double> {
     using Gas = TileCfg<32, 8, 2, false, false, 0>;
     using Bme = TileCfg<32, 4, 1, true, true, 4>;
 };
 
-// Launch geometry: the z-chunk height minimises (waves of resident blocks) x
-// (planes a block marches, including its 4-plane warm-up), using the kernel's
-// measured occupancy and the device's SM count.
+// Launch geometry.  tz > 0 (batched ensembles): a (tile, z chunk) grid of that
+// chunk height.  tz <= 0 (single grid): with C::BAL a balanced split -- one
+// block per resident slot (the kernel's occupancy times the SM count), each
+// taking an equal share of the tile-major (tile, plane) sequence, so no wave is
+// partly empty (at least 8 planes a block); else a (tile, chunk) grid whose
+// chunk height minimises waves x (chunk + 4).
 template <class P, typename T, class C>
 StepCfg make_cfg(int N, int tz) {
     StepCfg c;
@@ -38,11 +44,20 @@ StepCfg make_cfg(int N, int tz) {
         int dev = 0, sms = 152, per_sm = 1;
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_step_kernel<P, T, C, false>,
-                                                      c.threads, c.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_step_kernel<P, T, C, false>, c.threads,
+                                                      c.smem);
         if (per_sm < 1) per_sm = 1;
         const long slots = long(sms) * per_sm;
         const long tiles = long(c.tiles_x) * c.tiles_y;
+        if (C::BAL) {
+            long b = slots;
+            if (b > tiles * N / 8) b = tiles * N / 8;
+            if (b < 1) b = 1;
+            c.tz = 0;
+            c.blocks_z = 1;
+            c.balanced = int(b);
+            return c;
+        }
         long best = -1;
         for (int bz = 1; bz <= N / 8 || bz == 1; ++bz) {
             const int t = (N + bz - 1) / bz;
@@ -71,7 +86,7 @@ cudaError_t prepare() {
 template <class P, typename T, class C>
 cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
     BatchArgs<T> none{nullptr, nullptr};
-    const dim3 grid(c.tiles_x * c.tiles_y, c.blocks_z);
+    const dim3 grid = c.balanced > 0 ? dim3(c.balanced) : dim3(c.tiles_x * c.tiles_y, c.blocks_z);
     if (a.outflow)
         fluid_step_kernel<P, T, C, true><<<grid, c.threads, c.smem, st>>>(a, none);
     else

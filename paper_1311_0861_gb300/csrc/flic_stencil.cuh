@@ -48,8 +48,9 @@ struct StencilArgs {
     const T* phi;             // potential of the input state, N^3
     size_t fs;                // field stride in elements
     int n;                    // cells per axis
-    int tz;                   // z planes per block
-    int tiles_x;              // blocks along x (ceil(n / TX))
+    int tz;                   // z planes per block; 0: balanced split (below)
+    int tiles_x;              // tiles along x (ceil(n / TX))
+    int tiles_y;              // tiles along y (ceil(n / TY))
     int outflow;              // hydro boundaries: 0 periodic wrap, 1 zero-gradient ghost cells
     const double* tau;        // step size (device scalar)
     double inv_h;             // 1 / h
@@ -374,12 +375,15 @@ constexpr int RING_SLOTS = 3;   // planes e, e+1 in use, e+2 in flight
 // Launch shape of a fluid kernel: TX x TY column tile, minimum resident blocks
 // per SM (register budget), whether the moment energy tensor is staged in
 // shared memory (SEX), whether the block has one thread per updated cell (WIDE;
-// else one per tile cell, looping over the border cells) and how many x/y faces
-// each thread without a tile cell takes first (HR).
-template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_>
+// else one per tile cell, looping over the border cells), how many x/y faces
+// each thread without a tile cell takes first (HR) and whether a single grid is
+// split evenly over one block per resident slot (BAL) or as a (tile, z chunk)
+// grid (which keeps neighbouring tiles at the same planes, sharing their halos
+// in L2).
+template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_, bool BAL_ = false>
 struct TileCfg {
     static constexpr int TX = TX_, TY = TY_, MINB = MINB_, HR = HR_;
-    static constexpr bool SEX = SEX_, WIDE = WIDE_;
+    static constexpr bool SEX = SEX_, WIDE = WIDE_, BAL = BAL_;
 };
 
 template <class P, typename T, class C>
@@ -492,349 +496,377 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     int* xlast = yoff + H2;   // outflow: x of the last element of each chunk (ghost chunks repeat the edge)
 
     const int tid = threadIdx.x;
-    int tile, chunk, prow;
+    // Work of this block: one (tile, z chunk) of a batched work list or of the
+    // (tile, chunk) grid; or, with tz = 0, the block's equal share of the
+    // tile-major sequence of (tile, plane) updates, walked as segments that
+    // each lie in one tile column (a balanced split with one block per
+    // resident slot: no wave quantisation, two to three segments per block).
+    int tile = 0, prow, z0 = 0, z1 = 0;
+    long long u = 0, u_end = 0;
     StencilArgs<T> a;
     if (batch.work) {
         const WorkItem w = batch.work[blockIdx.x];
         a = batch.table[w.run];
         tile = w.tile;
-        chunk = w.chunk;
         prow = w.prow;
+        z0 = w.chunk * a.tz;
+        z1 = min(z0 + a.tz, a.n);
     } else {
         a = a1;
-        tile = blockIdx.x;
-        chunk = blockIdx.y;
-        prow = blockIdx.y * gridDim.x + blockIdx.x;
+        if (a.tz > 0) {
+            tile = blockIdx.x;
+            prow = blockIdx.y * gridDim.x + blockIdx.x;
+            z0 = blockIdx.y * a.tz;
+            z1 = min(z0 + a.tz, a.n);
+        } else {
+            const long long U = (long long)a.tiles_x * a.tiles_y * a.n;
+            u = U * blockIdx.x / gridDim.x;
+            u_end = U * (blockIdx.x + 1) / gridDim.x;
+            prow = blockIdx.x;
+            tile = int(u / a.n);
+            z0 = int(u % a.n);
+            z1 = (u_end - u < a.n - z0) ? z0 + int(u_end - u) : a.n;
+        }
     }
+    const bool balanced = !batch.work && a.tz <= 0;
     const int N = a.n;
     const size_t plane = size_t(N) * N;
-    const int x0 = (tile % a.tiles_x) * TX;
-    const int y0 = (tile / a.tiles_x) * TY;
-    const int z0 = chunk * a.tz;
-    const int z1 = min(z0 + a.tz, N);
     const T tau = T(*a.tau);
     const T rat = T(*a.tau * a.inv_h);
     const T half_ih = T(0.5 * a.inv_h);
     const T gamma = a.gamma, eta = a.eta;
-
-    // x0 - 2 and N are multiples of CH, so no chunk straddles the periodic wrap
-    // or the domain edge: with outflow a chunk lies inside the grid or wholly
-    // in the ghost layers (all its elements then copy one edge cell)
-    if constexpr (OUT) {
-        for (int i = tid; i < CPR; i += NTH) {
-            xoff[i] = min(max(x0 - 2 + CH * i, 0), N - 1);
-            xlast[i] = min(max(x0 - 2 + CH * i + CH - 1, 0), N - 1);
-        }
-        for (int i = tid; i < H2; i += NTH) yoff[i] = min(max(y0 + i - 2, 0), N - 1) * N;
-    } else {
-        for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
-        for (int i = tid; i < H2; i += NTH) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
-    }
-    __syncthreads();
-
-    // own tile cell (threads tid < NT)
-    const bool own_tile = tid < NT;
-    const int own_tx = own_tile ? tid % TX : 0, own_ty = own_tile ? tid / TX : 0;
-    const bool own_valid = own_tile && (x0 + own_tx < N) && (y0 + own_ty < N);
-    const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
-
-    // S0 of plane pz: asynchronous 8-byte copies of the ring fields of the plane
-    // (tile + 2-cell halo) into its ring slot, committed as one group.  Each
-    // thread owns fixed (row, chunk) positions and walks the fields.
-    constexpr int NPOS = H2 * CPR;
-    auto plane_of = [&](int pz) {
-        if constexpr (OUT) return min(max(pz, 0), N - 1);
-        return pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
-    };
-    // a ghost chunk at an outflow edge (its elements all copy one edge cell)
-    auto ghost_chunk = [&](int c) { return OUT && CH > 1 && xlast[c] != xoff[c] + CH - 1; };
-    auto issue_plane = [&](int pz) {
-        T* dst = ring + ring_slot(pz) * NR * R2;
-        const size_t zoff = size_t(plane_of(pz)) * plane;
-        for (int pos = tid; pos < NPOS; pos += NTH) {
-            const int iy = pos / CPR, c = pos % CPR;
-            T* d = dst + iy * W2 + c * CH;
-            const size_t goff = zoff + size_t(yoff[iy]) + xoff[c];
-            const T* src = a.in + goff;
-            if (ghost_chunk(c)) {
-                // plain loads (visible after the barrier that precedes this
-                // slot's first use, like the asynchronous copies)
-#pragma unroll
-                for (int r = 0; r < NR - 1; ++r) {
-                    const T v = __ldg(src + size_t(P::ring_field(r)) * a.fs);
-#pragma unroll
-                    for (int k = 0; k < CH; ++k) d[r * R2 + k] = v;
-                }
-                const T v = __ldg(a.phi + goff);
-#pragma unroll
-                for (int k = 0; k < CH; ++k) d[(NR - 1) * R2 + k] = v;
-                continue;
-            }
-#pragma unroll
-            for (int r = 0; r < NR - 1; ++r) cp_async8(d + r * R2, src + size_t(P::ring_field(r)) * a.fs);
-            cp_async8(d + (NR - 1) * R2, a.phi + goff);
-        }
-        cp_async_commit();
-    };
-    // extra fields of plane pz over the R1 rows into slot pz & 1 (same group as
-    // the ring copy issued in the same iteration)
-    constexpr int NPOS1 = Gm::H1 * CPR;
-    auto issue_extra = [&](int pz) {
-        T* dst = exb + (pz & 1) * Gm::ex_slot;
-        const size_t zoff = size_t(plane_of(pz)) * plane;
-        for (int pos = tid; pos < NPOS1; pos += NTH) {
-            const int jy = pos / CPR, c = pos % CPR;
-            T* d = dst + jy * W2 + c * CH;
-            const T* src = a.in + zoff + size_t(yoff[jy + 1]) + xoff[c];
-            if (ghost_chunk(c)) {
-#pragma unroll
-                for (int k = 0; k < NEX; ++k) {
-                    const T v = __ldg(src + size_t(P::extra_field(k)) * a.fs);
-#pragma unroll
-                    for (int j = 0; j < CH; ++j) d[k * Gm::H1 * W2 + j] = v;
-                }
-                continue;
-            }
-#pragma unroll
-            for (int k = 0; k < NEX; ++k)
-                cp_async8(d + k * Gm::H1 * W2, src + size_t(P::extra_field(k)) * a.fs);
-        }
-    };
-    // global x of R2 column ix (chunks never straddle the wrap or the edge)
-    auto gx = [&](int ix) {
-        if constexpr (OUT) return ghost_chunk(ix / CH) ? xoff[ix / CH] : xoff[ix / CH] + ix % CH;
-        return xoff[ix / CH] + ix % CH;
-    };
-
-    const size_t own_g = size_t(yoff[own_ty + 2]) + gx(own_tx + 2);
-    T fprev[NF], acc[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); }
-    T wz_prev = T(0);
     Acc<T> q[P::NQ];
     T vmax = T(0);
     bool bad = false;
 
-    // Fields the Eulerian update reads straight from global memory (SEX false):
-    // with one updated cell per thread (NTH >= NU) each thread keeps its cell
-    // for the whole march, so the next plane's values are loaded into
-    // registers one iteration ahead and their latency hides behind a plane.
-    constexpr bool PREF = !SEX && NEX > 0 && NTH >= NU;
-    T exn[NEX > 0 ? NEX : 1];
-    size_t my_g = 0;
-    if constexpr (PREF) {
-        if (tid < NU) {
-            int jx, jy;
-            r1_coords<TX, TY>(tid, jx, jy);
-            my_g = size_t(yoff[jy + 1]) + gx(jx + 1);
-        }
-    }
-    auto load_ex = [&](int pz) {
-        const size_t g = size_t(plane_of(pz)) * plane + my_g;
-#pragma unroll
-        for (int k = 0; k < NEX; ++k) exn[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
-    };
-    if constexpr (PREF) {
-        if (tid < NU) load_ex(z0 - 1);   // the first plane whose update is needed
-    }
+    while (z1 > z0) {   // one segment: a column of planes [z0, z1) of one tile
+        const int x0 = (tile % a.tiles_x) * TX;
+        const int y0 = (tile / a.tiles_x) * TY;
 
-    // x / y face solutions of plane pe over the tile + 1-cell halo (S1).  The
-    // helpers take the first NH * HR faces (they have no S3 work); the rest go
-    // round-robin over all threads.
-    constexpr int NH = NTH - NT;
-    constexpr int HF = (NH * C::HR < NXF + NYF) ? NH * C::HR : NXF + NYF;
-    auto face_item = [&](const T* rpe, int i) {
-        T v[NFACE];
-        if (i < NXF) {
-            const int fx = i % Gm::XFW, jy = i / Gm::XFW;
-            const int a2 = (jy + 1) * W2 + fx;
-            P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
-#pragma unroll
-            for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
+        // x0 - 2 and N are multiples of CH, so no chunk straddles the periodic wrap
+        // or the domain edge: with outflow a chunk lies inside the grid or wholly
+        // in the ghost layers (all its elements then copy one edge cell)
+        if constexpr (OUT) {
+            for (int i = tid; i < CPR; i += NTH) {
+                xoff[i] = min(max(x0 - 2 + CH * i, 0), N - 1);
+                xlast[i] = min(max(x0 - 2 + CH * i + CH - 1, 0), N - 1);
+            }
+            for (int i = tid; i < H2; i += NTH) yoff[i] = min(max(y0 + i - 2, 0), N - 1) * N;
         } else {
-            const int j = i - NXF;
-            const int jx = j % W1, fy = j / W1;
-            const int a2 = fy * W2 + jx + 1;
-            P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
-#pragma unroll
-            for (int k = 0; k < NFACE; ++k) yf[k * NYF + j] = v[k];
-        }
-    };
-    auto xy_faces = [&](const T* rpe) {
-        if constexpr (NH > 0) {
-            if (!own_tile)
-                for (int i = tid - NT; i < HF; i += NH) face_item(rpe, i);
-        }
-        for (int i = HF + tid; i < NXF + NYF; i += NTH) face_item(rpe, i);
-    };
-
-    // Two barriers per plane.  Iteration e:
-    //   [copies of planes e, e+1 landed; barrier]
-    //   phase 1: z faces e+1/2 and the Eulerian update of plane e over R1 (S2)
-    //   [barrier]
-    //   phase 2: Lagrangian fluxes of the own cell at plane e (S3), then the x/y
-    //            faces of plane e+1 (S1) -- the own cell's face velocities were
-    //            kept in registers in phase 1, so the face buffers can be reused
-    issue_plane(z0 - 2);
-    issue_plane(z0 - 1);
-    T Wxm = T(0), Wxp = T(0), Wym = T(0), Wyp = T(0);
-    for (int e = z0 - 2; e <= z1; ++e) {
-        const T* re = ring + ring_slot(e) * NR * R2;       // plane e
-        const T* rp = ring + ring_slot(e + 1) * NR * R2;   // plane e + 1
-        // plane e + 2 goes into the slot of plane e - 1 (last read in phase 1
-        // of the previous iteration); the staged extra fields of plane e + 1
-        // (read in phase 1 of the next iteration) travel in the same group
-        if (e + 2 <= z1 + 1) {
-            if (SEX && NEX > 0 && e + 1 >= z0 - 1) issue_extra(e + 1);
-            issue_plane(e + 2);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+            for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
+            for (int i = tid; i < H2; i += NTH) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
         }
         __syncthreads();
-        const bool active = (e >= z0 - 1);   // f' of plane e is needed
-        // ---- phase 1: z face e+1/2 and Eulerian update of plane e over R1 ----
-        {
-            const size_t zoff_e = size_t(plane_of(e)) * plane;
-            for (int i = tid; i < NU; i += NTH) {
+
+        // own tile cell (threads tid < NT)
+        const bool own_tile = tid < NT;
+        const int own_tx = own_tile ? tid % TX : 0, own_ty = own_tile ? tid / TX : 0;
+        const bool own_valid = own_tile && (x0 + own_tx < N) && (y0 + own_ty < N);
+        const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
+
+        // S0 of plane pz: asynchronous 8-byte copies of the ring fields of the plane
+        // (tile + 2-cell halo) into its ring slot, committed as one group.  Each
+        // thread owns fixed (row, chunk) positions and walks the fields.
+        constexpr int NPOS = H2 * CPR;
+        auto plane_of = [&](int pz) {
+            if constexpr (OUT) return min(max(pz, 0), N - 1);
+            return pz < 0 ? pz + N : (pz >= N ? pz - N : pz);
+        };
+        // a ghost chunk at an outflow edge (its elements all copy one edge cell)
+        auto ghost_chunk = [&](int c) { return OUT && CH > 1 && xlast[c] != xoff[c] + CH - 1; };
+        auto issue_plane = [&](int pz) {
+            T* dst = ring + ring_slot(pz) * NR * R2;
+            const size_t zoff = size_t(plane_of(pz)) * plane;
+            for (int pos = tid; pos < NPOS; pos += NTH) {
+                const int iy = pos / CPR, c = pos % CPR;
+                T* d = dst + iy * W2 + c * CH;
+                const size_t goff = zoff + size_t(yoff[iy]) + xoff[c];
+                const T* src = a.in + goff;
+                if (ghost_chunk(c)) {
+                    // plain loads (visible after the barrier that precedes this
+                    // slot's first use, like the asynchronous copies)
+#pragma unroll
+                    for (int r = 0; r < NR - 1; ++r) {
+                        const T v = __ldg(src + size_t(P::ring_field(r)) * a.fs);
+#pragma unroll
+                        for (int k = 0; k < CH; ++k) d[r * R2 + k] = v;
+                    }
+                    const T v = __ldg(a.phi + goff);
+#pragma unroll
+                    for (int k = 0; k < CH; ++k) d[(NR - 1) * R2 + k] = v;
+                    continue;
+                }
+#pragma unroll
+                for (int r = 0; r < NR - 1; ++r) cp_async8(d + r * R2, src + size_t(P::ring_field(r)) * a.fs);
+                cp_async8(d + (NR - 1) * R2, a.phi + goff);
+            }
+            cp_async_commit();
+        };
+        // extra fields of plane pz over the R1 rows into slot pz & 1 (same group as
+        // the ring copy issued in the same iteration)
+        constexpr int NPOS1 = Gm::H1 * CPR;
+        auto issue_extra = [&](int pz) {
+            T* dst = exb + (pz & 1) * Gm::ex_slot;
+            const size_t zoff = size_t(plane_of(pz)) * plane;
+            for (int pos = tid; pos < NPOS1; pos += NTH) {
+                const int jy = pos / CPR, c = pos % CPR;
+                T* d = dst + jy * W2 + c * CH;
+                const T* src = a.in + zoff + size_t(yoff[jy + 1]) + xoff[c];
+                if (ghost_chunk(c)) {
+#pragma unroll
+                    for (int k = 0; k < NEX; ++k) {
+                        const T v = __ldg(src + size_t(P::extra_field(k)) * a.fs);
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) d[k * Gm::H1 * W2 + j] = v;
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int k = 0; k < NEX; ++k)
+                    cp_async8(d + k * Gm::H1 * W2, src + size_t(P::extra_field(k)) * a.fs);
+            }
+        };
+        // global x of R2 column ix (chunks never straddle the wrap or the edge)
+        auto gx = [&](int ix) {
+            if constexpr (OUT) return ghost_chunk(ix / CH) ? xoff[ix / CH] : xoff[ix / CH] + ix % CH;
+            return xoff[ix / CH] + ix % CH;
+        };
+
+        const size_t own_g = size_t(yoff[own_ty + 2]) + gx(own_tx + 2);
+        T fprev[NF], acc[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) { fprev[f] = T(0); acc[f] = T(0); }
+        T wz_prev = T(0);
+
+        // Fields the Eulerian update reads straight from global memory (SEX false):
+        // with one updated cell per thread (NTH >= NU) each thread keeps its cell
+        // for the whole march, so the next plane's values are loaded into
+        // registers one iteration ahead and their latency hides behind a plane.
+        constexpr bool PREF = !SEX && NEX > 0 && NTH >= NU;
+        T exn[NEX > 0 ? NEX : 1];
+        size_t my_g = 0;
+        if constexpr (PREF) {
+            if (tid < NU) {
                 int jx, jy;
-                r1_coords<TX, TY>(i, jx, jy);
-                const int c1 = jy * W1 + jx;
-                const int c2 = (jy + 1) * W2 + jx + 1;
-                T ex[NEX > 0 ? NEX : 1];
-                if (active) {
-                    if constexpr (PREF) {
-#pragma unroll
-                        for (int k = 0; k < NEX; ++k) ex[k] = exn[k];
-                        if (e + 1 <= z1) load_ex(e + 1);
-                    } else if (SEX) {
-                        const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
-#pragma unroll
-                        for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
-                    } else {
-                        const size_t g = zoff_e + size_t(yoff[jy + 1]) + gx(jx + 1);
-#pragma unroll
-                        for (int k = 0; k < NEX; ++k) ex[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
-                    }
-                }
-                T zn[NFACE];
-                P::face(re, c2, rp, c2, R2, 2, gamma, zn);
-                if (active) {
-                    T fm[3][NFACE], fpv[3][NFACE];
-#pragma unroll
-                    for (int k = 0; k < NFACE; ++k) {
-                        fm[0][k] = xf[k * NXF + jy * Gm::XFW + jx];
-                        fpv[0][k] = xf[k * NXF + jy * Gm::XFW + jx + 1];
-                        fm[1][k] = yf[k * NYF + jy * W1 + jx];
-                        fpv[1][k] = yf[k * NYF + (jy + 1) * W1 + jx];
-                        fm[2][k] = zc[k * R1 + c1];
-                        fpv[2][k] = zn[k];
-                    }
-                    T g[3];
-                    g[0] = (re[P::R_PHI * R2 + c2 + 1] - re[P::R_PHI * R2 + c2 - 1]) * half_ih;
-                    g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
-                    g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
-                    T f1[NF];
-                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
-#pragma unroll
-                    if constexpr (FP2) {
-                        // field pairs side by side: one 8-byte store per pair
-#pragma unroll
-                        for (int f = 0; f < NF; f += 2)
-                            reinterpret_cast<float2*>(fpb)[(f / 2) * R1 + c1] = make_float2(f1[f], f1[f + 1]);
-                    } else {
-#pragma unroll
-                        for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
-                    }
-                    if (i < NT) {
-                        // own tile cell (i == tid): keep its face normal velocities for phase 2
-                        // (gas: V first on every axis; moments: u*_d is value d)
-                        wz_prev = P::normal_velocity(fm[2], 2);
-                        Wxm = P::normal_velocity(fm[0], 0);
-                        Wxp = P::normal_velocity(fpv[0], 0);
-                        Wym = P::normal_velocity(fm[1], 1);
-                        Wyp = P::normal_velocity(fpv[1], 1);
-                        if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
-                phim[c1] = re[P::R_PHI * R2 + c2];
+                r1_coords<TX, TY>(tid, jx, jy);
+                my_g = size_t(yoff[jy + 1]) + gx(jx + 1);
             }
         }
-        __syncthreads();
-        // ---- phase 2: Lagrangian fluxes of the own tile cell (plane e) -----
-        if (active && own_tile) {
-            const T Wzm = wz_prev;
-            // upwind cell of each lateral face (the own cell where the face
-            // velocity points away from it)
-            const int cxm = own_c1 - (Wxm > T(0) ? 1 : 0);
-            const int cxp = own_c1 + (Wxp > T(0) ? 0 : 1);
-            const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
-            const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
-            T out[NF];
-            if constexpr (PK) {
-                // fields in pairs with packed float32 arithmetic (one instruction
-                // for two fields); the same operations as the scalar form below
-                const float2 wz = make_float2(Wzm, Wzm), nr = make_float2(-rat, -rat), pr = make_float2(rat, rat);
-                const float2 wxp = make_float2(Wxp, Wxp), nwxm = make_float2(-Wxm, -Wxm);
-                const float2 wyp = make_float2(Wyp, Wyp), nwym = make_float2(-Wym, -Wym);
-                const bool zup = Wzm > T(0);
+        auto load_ex = [&](int pz) {
+            const size_t g = size_t(plane_of(pz)) * plane + my_g;
 #pragma unroll
-                for (int f = 0; f < NF; f += 2) {
-                    float2 fc, uxm, uxp, uym, uyp;
-                    if constexpr (FP2) {
-                        const float2* F2 = reinterpret_cast<const float2*>(fpb) + (f / 2) * R1;
-                        fc = F2[own_c1];
-                        uxm = F2[cxm];
-                        uxp = F2[cxp];
-                        uym = F2[cym];
-                        uyp = F2[cyp];
-                    } else {
-                        const T* F0 = fpb + f * R1;
-                        const T* F1 = F0 + R1;
-                        fc = make_float2(F0[own_c1], F1[own_c1]);
-                        uxm = make_float2(F0[cxm], F1[cxm]);
-                        uxp = make_float2(F0[cxp], F1[cxp]);
-                        uym = make_float2(F0[cym], F1[cym]);
-                        uyp = make_float2(F0[cyp], F1[cyp]);
-                    }
-                    const float2 Fzm = __fmul2_rn(wz, zup ? make_float2(fprev[f], fprev[f + 1]) : fc);
-                    const float2 o = __ffma2_rn(nr, Fzm, make_float2(acc[f], acc[f + 1]));   // completes plane e-1
-                    float2 t = __fadd2_rn(__ffma2_rn(nwxm, uxm, __fmul2_rn(wxp, uxp)),
-                                          __ffma2_rn(nwym, uym, __fmul2_rn(wyp, uyp)));
-                    const float2 n2 = __ffma2_rn(pr, Fzm, __ffma2_rn(nr, t, fc));
-                    out[f] = o.x;
-                    out[f + 1] = o.y;
-                    acc[f] = n2.x;
-                    acc[f + 1] = n2.y;
-                    fprev[f] = fc.x;
-                    fprev[f + 1] = fc.y;
-                }
+            for (int k = 0; k < NEX; ++k) exn[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
+        };
+        if constexpr (PREF) {
+            if (tid < NU) load_ex(z0 - 1);   // the first plane whose update is needed
+        }
+
+        // x / y face solutions of plane pe over the tile + 1-cell halo (S1).  The
+        // helpers take the first NH * HR faces (they have no S3 work); the rest go
+        // round-robin over all threads.
+        constexpr int NH = NTH - NT;
+        constexpr int HF = (NH * C::HR < NXF + NYF) ? NH * C::HR : NXF + NYF;
+        auto face_item = [&](const T* rpe, int i) {
+            T v[NFACE];
+            if (i < NXF) {
+                const int fx = i % Gm::XFW, jy = i / Gm::XFW;
+                const int a2 = (jy + 1) * W2 + fx;
+                P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
             } else {
+                const int j = i - NXF;
+                const int jx = j % W1, fy = j / W1;
+                const int a2 = fy * W2 + jx + 1;
+                P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const T* F = fpb + f * R1;
-                    const T fc = F[own_c1];
-                    const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
-                    const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
-                    out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
-                    acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
-                    fprev[f] = fc;
+                for (int k = 0; k < NFACE; ++k) yf[k * NYF + j] = v[k];
+            }
+        };
+        auto xy_faces = [&](const T* rpe) {
+            if constexpr (NH > 0) {
+                if (!own_tile)
+                    for (int i = tid - NT; i < HF; i += NH) face_item(rpe, i);
+            }
+            for (int i = HF + tid; i < NXF + NYF; i += NTH) face_item(rpe, i);
+        };
+
+        // Two barriers per plane.  Iteration e:
+        //   [copies of planes e, e+1 landed; barrier]
+        //   phase 1: z faces e+1/2 and the Eulerian update of plane e over R1 (S2)
+        //   [barrier]
+        //   phase 2: Lagrangian fluxes of the own cell at plane e (S3), then the x/y
+        //            faces of plane e+1 (S1) -- the own cell's face velocities were
+        //            kept in registers in phase 1, so the face buffers can be reused
+        issue_plane(z0 - 2);
+        issue_plane(z0 - 1);
+        T Wxm = T(0), Wxp = T(0), Wym = T(0), Wyp = T(0);
+        for (int e = z0 - 2; e <= z1; ++e) {
+            const T* re = ring + ring_slot(e) * NR * R2;       // plane e
+            const T* rp = ring + ring_slot(e + 1) * NR * R2;   // plane e + 1
+            // plane e + 2 goes into the slot of plane e - 1 (last read in phase 1
+            // of the previous iteration); the staged extra fields of plane e + 1
+            // (read in phase 1 of the next iteration) travel in the same group
+            if (e + 2 <= z1 + 1) {
+                if (SEX && NEX > 0 && e + 1 >= z0 - 1) issue_extra(e + 1);
+                issue_plane(e + 2);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const bool active = (e >= z0 - 1);   // f' of plane e is needed
+            // ---- phase 1: z face e+1/2 and Eulerian update of plane e over R1 ----
+            {
+                const size_t zoff_e = size_t(plane_of(e)) * plane;
+                for (int i = tid; i < NU; i += NTH) {
+                    int jx, jy;
+                    r1_coords<TX, TY>(i, jx, jy);
+                    const int c1 = jy * W1 + jx;
+                    const int c2 = (jy + 1) * W2 + jx + 1;
+                    T ex[NEX > 0 ? NEX : 1];
+                    if (active) {
+                        if constexpr (PREF) {
+#pragma unroll
+                            for (int k = 0; k < NEX; ++k) ex[k] = exn[k];
+                            if (e + 1 <= z1) load_ex(e + 1);
+                        } else if (SEX) {
+                            const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
+#pragma unroll
+                            for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
+                        } else {
+                            const size_t g = zoff_e + size_t(yoff[jy + 1]) + gx(jx + 1);
+#pragma unroll
+                            for (int k = 0; k < NEX; ++k) ex[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
+                        }
+                    }
+                    T zn[NFACE];
+                    P::face(re, c2, rp, c2, R2, 2, gamma, zn);
+                    if (active) {
+                        T fm[3][NFACE], fpv[3][NFACE];
+#pragma unroll
+                        for (int k = 0; k < NFACE; ++k) {
+                            fm[0][k] = xf[k * NXF + jy * Gm::XFW + jx];
+                            fpv[0][k] = xf[k * NXF + jy * Gm::XFW + jx + 1];
+                            fm[1][k] = yf[k * NYF + jy * W1 + jx];
+                            fpv[1][k] = yf[k * NYF + (jy + 1) * W1 + jx];
+                            fm[2][k] = zc[k * R1 + c1];
+                            fpv[2][k] = zn[k];
+                        }
+                        T g[3];
+                        g[0] = (re[P::R_PHI * R2 + c2 + 1] - re[P::R_PHI * R2 + c2 - 1]) * half_ih;
+                        g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
+                        g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
+                        T f1[NF];
+                        P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
+#pragma unroll
+                        if constexpr (FP2) {
+                            // field pairs side by side: one 8-byte store per pair
+#pragma unroll
+                            for (int f = 0; f < NF; f += 2)
+                                reinterpret_cast<float2*>(fpb)[(f / 2) * R1 + c1] = make_float2(f1[f], f1[f + 1]);
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
+                        }
+                        if (i < NT) {
+                            // own tile cell (i == tid): keep its face normal velocities for phase 2
+                            // (gas: V first on every axis; moments: u*_d is value d)
+                            wz_prev = P::normal_velocity(fm[2], 2);
+                            Wxm = P::normal_velocity(fm[0], 0);
+                            Wxp = P::normal_velocity(fpv[0], 0);
+                            Wym = P::normal_velocity(fm[1], 1);
+                            Wyp = P::normal_velocity(fpv[1], 1);
+                            if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
+                    phim[c1] = re[P::R_PHI * R2 + c2];
                 }
             }
-            const int l = e - 1;
-            if (l >= z0 && l < z1 && own_valid) {
-                P::finish(out, gamma, eta, q, vmax, bad);
-                const size_t g = size_t(l) * plane + own_g;
+            __syncthreads();
+            // ---- phase 2: Lagrangian fluxes of the own tile cell (plane e) -----
+            if (active && own_tile) {
+                const T Wzm = wz_prev;
+                // upwind cell of each lateral face (the own cell where the face
+                // velocity points away from it)
+                const int cxm = own_c1 - (Wxm > T(0) ? 1 : 0);
+                const int cxp = own_c1 + (Wxp > T(0) ? 0 : 1);
+                const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
+                const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
+                T out[NF];
+                if constexpr (PK) {
+                    // fields in pairs with packed float32 arithmetic (one instruction
+                    // for two fields); the same operations as the scalar form below
+                    const float2 wz = make_float2(Wzm, Wzm), nr = make_float2(-rat, -rat), pr = make_float2(rat, rat);
+                    const float2 wxp = make_float2(Wxp, Wxp), nwxm = make_float2(-Wxm, -Wxm);
+                    const float2 wyp = make_float2(Wyp, Wyp), nwym = make_float2(-Wym, -Wym);
+                    const bool zup = Wzm > T(0);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) __stcs(a.out + f * a.fs + g, out[f]);   // streaming global store
+                    for (int f = 0; f < NF; f += 2) {
+                        float2 fc, uxm, uxp, uym, uyp;
+                        if constexpr (FP2) {
+                            const float2* F2 = reinterpret_cast<const float2*>(fpb) + (f / 2) * R1;
+                            fc = F2[own_c1];
+                            uxm = F2[cxm];
+                            uxp = F2[cxp];
+                            uym = F2[cym];
+                            uyp = F2[cyp];
+                        } else {
+                            const T* F0 = fpb + f * R1;
+                            const T* F1 = F0 + R1;
+                            fc = make_float2(F0[own_c1], F1[own_c1]);
+                            uxm = make_float2(F0[cxm], F1[cxm]);
+                            uxp = make_float2(F0[cxp], F1[cxp]);
+                            uym = make_float2(F0[cym], F1[cym]);
+                            uyp = make_float2(F0[cyp], F1[cyp]);
+                        }
+                        const float2 Fzm = __fmul2_rn(wz, zup ? make_float2(fprev[f], fprev[f + 1]) : fc);
+                        const float2 o = __ffma2_rn(nr, Fzm, make_float2(acc[f], acc[f + 1]));   // completes plane e-1
+                        float2 t = __fadd2_rn(__ffma2_rn(nwxm, uxm, __fmul2_rn(wxp, uxp)),
+                                              __ffma2_rn(nwym, uym, __fmul2_rn(wyp, uyp)));
+                        const float2 n2 = __ffma2_rn(pr, Fzm, __ffma2_rn(nr, t, fc));
+                        out[f] = o.x;
+                        out[f + 1] = o.y;
+                        acc[f] = n2.x;
+                        acc[f + 1] = n2.y;
+                        fprev[f] = fc.x;
+                        fprev[f + 1] = fc.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const T* F = fpb + f * R1;
+                        const T fc = F[own_c1];
+                        const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
+                        const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
+                        out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
+                        acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
+                        fprev[f] = fc;
+                    }
+                }
+                const int l = e - 1;
+                if (l >= z0 && l < z1 && own_valid) {
+                    P::finish(out, gamma, eta, q, vmax, bad);
+                    const size_t g = size_t(l) * plane + own_g;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) __stcs(a.out + f * a.fs + g, out[f]);   // streaming global store
+                }
             }
+            // ---- phase 2: x/y faces of plane e + 1 ----------------------------
+            if (e + 1 <= z1) xy_faces(rp);
         }
-        // ---- phase 2: x/y faces of plane e + 1 ----------------------------
-        if (e + 1 <= z1) xy_faces(rp);
+        cp_async_wait<0>();
+        // next segment (balanced split only): the next tile's column from plane 0
+        if (!balanced) break;
+        u += z1 - z0;
+        if (u >= u_end) break;
+        ++tile;
+        z0 = 0;
+        z1 = (u_end - u < N) ? int(u_end - u) : N;
+        __syncthreads();   // the ring and the coordinate tables are reused
     }
-    cp_async_wait<0>();
 
     // ---- block reduction of the conserved sums, kappa and the signal speed ----
     const int lane = tid & 31, warp = tid >> 5;
