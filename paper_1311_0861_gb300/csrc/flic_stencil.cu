@@ -13,9 +13,11 @@ template <typename T> struct Tiles;
 // each first), one block per SM and no register cap -- faster than 256-thread
 // blocks two per SM, whose 128-register cap spills and whose border cells take
 // a second phase-1 round (helper rounds 5 / 6 / 7: 1.153 / 1.164 / 1.175 ms);
-// the balanced split over its 152 resident blocks beats the chunked grid
-// (1.099 vs 1.154 ms), while the gas kernel keeps the chunked grid (0.473 vs
-// 0.492 ms balanced: its neighbouring tiles then share halos in L2).
+// the balanced split over its 152 resident blocks (whole tile columns in
+// lockstep rounds, then an even share of the rest) beats the chunked grid
+// (1.083 vs 1.154 ms; DRAM traffic 1.18x the compulsory bytes, vs 2.46x for a
+// plain tile-major share, whose concurrent blocks no longer share halos in
+// L2), while the gas kernel keeps the chunked grid (0.473 vs 0.492 ms).
 template <> struct Tiles<float> {
     using Gas = TileCfg<32, 8, 3, false, false, 0>;
     using Bme = TileCfg<32, 12, 1, false, true, 5, true>;

@@ -497,12 +497,15 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
 
     const int tid = threadIdx.x;
     // Work of this block: one (tile, z chunk) of a batched work list or of the
-    // (tile, chunk) grid; or, with tz = 0, the block's equal share of the
-    // tile-major sequence of (tile, plane) updates, walked as segments that
-    // each lie in one tile column (a balanced split with one block per
-    // resident slot: no wave quantisation, two to three segments per block).
+    // (tile, chunk) grid; or, with tz = 0, a balanced split over B blocks (one
+    // per resident slot): F = T / B rounds of whole tile columns (block b takes
+    // tiles b, b + B, ...; all blocks march the same planes, so neighbouring
+    // tiles share their halos in L2), then an equal share of the tile-major
+    // (tile, plane) sequence of the remaining T - F B tiles, walked as segments
+    // that each lie in one tile column.
     int tile = 0, prow, z0 = 0, z1 = 0;
-    long long u = 0, u_end = 0;
+    long long u = 0, u_end = 0;   // remainder range, in plane updates
+    int round = 0, full_rounds = 0;
     StencilArgs<T> a;
     if (batch.work) {
         const WorkItem w = batch.work[blockIdx.x];
@@ -519,13 +522,22 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             z0 = blockIdx.y * a.tz;
             z1 = min(z0 + a.tz, a.n);
         } else {
-            const long long U = (long long)a.tiles_x * a.tiles_y * a.n;
+            const int ntiles = a.tiles_x * a.tiles_y;
+            full_rounds = ntiles / int(gridDim.x);
+            const long long U = (long long)(ntiles - full_rounds * int(gridDim.x)) * a.n;
             u = U * blockIdx.x / gridDim.x;
             u_end = U * (blockIdx.x + 1) / gridDim.x;
             prow = blockIdx.x;
-            tile = int(u / a.n);
-            z0 = int(u % a.n);
-            z1 = (u_end - u < a.n - z0) ? z0 + int(u_end - u) : a.n;
+            if (full_rounds > 0) {
+                tile = blockIdx.x;
+                z0 = 0;
+                z1 = a.n;
+                round = 1;
+            } else {
+                tile = int(u / a.n);
+                z0 = int(u % a.n);
+                z1 = (u_end - u < a.n - z0) ? z0 + int(u_end - u) : a.n;
+            }
         }
     }
     const bool balanced = !batch.work && a.tz <= 0;
@@ -858,13 +870,29 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             if (e + 1 <= z1) xy_faces(rp);
         }
         cp_async_wait<0>();
-        // next segment (balanced split only): the next tile's column from plane 0
+        // next segment (balanced split only)
         if (!balanced) break;
-        u += z1 - z0;
-        if (u >= u_end) break;
-        ++tile;
-        z0 = 0;
-        z1 = (u_end - u < N) ? int(u_end - u) : N;
+        if (round > 0 && round < full_rounds) {           // next whole tile column
+            tile = blockIdx.x + round * int(gridDim.x);
+            z0 = 0;
+            z1 = N;
+            ++round;
+        } else {
+            if (round > 0) {                               // whole columns done: the remainder share
+                round = 0;
+                if (u >= u_end) break;
+                const long long rt = u / N;
+                tile = full_rounds * int(gridDim.x) + int(rt);
+                z0 = int(u - rt * N);
+                z1 = (u_end - u < N - z0) ? z0 + int(u_end - u) : N;
+            } else {                                       // within the remainder share
+                u += z1 - z0;
+                if (u >= u_end) break;
+                ++tile;
+                z0 = 0;
+                z1 = (u_end - u < N) ? int(u_end - u) : N;
+            }
+        }
         __syncthreads();   // the ring and the coordinate tables are reused
     }
 
