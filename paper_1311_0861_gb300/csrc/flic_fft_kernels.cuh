@@ -6,9 +6,11 @@
 //   never written back).
 //
 // Each pass is one HBM read and one write of the spectrum.  In-block transforms
-// are Stockham autosort with radix-4, then 2, then 3 butterflies; the radix
-// sequence, strides and index arithmetic are compile-time; twiddles are staged
-// in shared memory from a table exp(-2 pi i j / L), j < L.
+// are Stockham autosort, in place in one shared buffer (each thread holds its
+// butterflies' 16 elements in registers across a barrier), with radix 16 first,
+// then 8, 4, 2 and 3; the radix sequence, strides and index arithmetic are
+// compile-time; twiddles are staged in shared memory from a table
+// exp(-2 pi i j / L), j < L.
 //
 // Spectrum layout: S[z][y][kx], z < P (only physical z planes are ever held),
 // y < L, kx < L/2 + 1 (kx fastest).
@@ -151,54 +153,11 @@ template <int L> struct RadixIP {
 };
 
 // One Stockham pass of radix R at span NS over NL lines of length L held in
-// shared memory; element (line l, index j) at buf[j * SJ + l * SL].  Twiddle
-// exp(-2 pi i m / TWL) is tw[m] (TWL a multiple of L).
-template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int R, int TWL>
-__device__ __forceinline__ void stockham_pass(const C* __restrict__ A, C* __restrict__ B, const C* tw) {
-    constexpr int NB = L / R;
-    constexpr int TOTAL = NB * NL;
-    constexpr int TSC = (TWL / L) * (L / (NS * R));
-    for (int t = threadIdx.x; t < TOTAL; t += blockDim.x) {
-        const int l = LFAST ? t % NL : t / NB;
-        const int j = LFAST ? t / NL : t % NB;
-        const int k = j % NS;
-        C x[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = A[(j + q * NB) * SJ + l * SL];
-        if (NS > 1) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) {
-                C w = tw[q * k * TSC];
-                if (INV) w.y = -w.y;
-                x[q] = cmul(x[q], w);
-            }
-        }
-        Butterfly<C, INV, R>::run(x);
-        const int idx = (j / NS) * NS * R + k;
-#pragma unroll
-        for (int q = 0; q < R; ++q) B[(idx + q * NS) * SJ + l * SL] = x[q];
-    }
-}
-
-template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int REM, int TWL>
-struct Stockham {
-    static __device__ __forceinline__ C* run(C* A, C* B, const C* tw) {
-        constexpr int R = FirstRadix<REM>::value;
-        static_assert(R > 1, "transform length must be 2^a 3^b");
-        stockham_pass<C, INV, L, NL, SJ, SL, LFAST, NS, R, TWL>(A, B, tw);
-        __syncthreads();
-        return Stockham<C, INV, L, NL, SJ, SL, LFAST, NS * R, REM / R, TWL>::run(B, A, tw);
-    }
-};
-template <typename C, bool INV, int L, int NL, int SJ, int SL, bool LFAST, int NS, int TWL>
-struct Stockham<C, INV, L, NL, SJ, SL, LFAST, NS, 1, TWL> {
-    static __device__ __forceinline__ C* run(C* A, C*, const C*) { return A; }
-};
-
-// In-place Stockham pass for a block of exactly NTHR threads: every thread
-// reads the inputs of its butterflies into registers, the block synchronises,
-// then the outputs overwrite the same buffer (one buffer instead of two, so
-// twice the lines fit in shared memory).
+// shared memory, element (line l, index j) at A[j * SJ + l * SL], twiddle
+// exp(-2 pi i m / TWL) at tw[m] (TWL a multiple of L); in place, for a block of
+// exactly NTHR threads: every thread reads the inputs of its butterflies into
+// registers, the block synchronises, then the outputs overwrite the same
+// buffer (one buffer instead of two, so twice the lines fit in shared memory).
 // HALF bit 0: the line's second half is zero (zero-padded input), so the first
 // pass (span 1) skips loading it; bit 1: only the first half of the result is
 // wanted, so the last pass (span L/R) stores only its first R/2 outputs.
