@@ -12,12 +12,13 @@
 //     moments take Pi = nE - q q^T/n when its trace is >= eta tr(nE) and its
 //     diagonal is positive, else reset nE = Pi + q q^T/n.
 //
-// Structure (2.5D z-march).  A block owns a TX x TY column tile and a chunk of
-// z planes.  It walks up the chunk with a ring of input planes in shared memory
-// over the tile plus a 2-cell halo (R2).  Thread i < TX*TY owns tile column i;
-// the block has one thread per cell of the tile and its four 1-cell edge
-// strips (rounded up to whole warps), so the Eulerian update of a plane is one
-// item per thread.  Per plane e (two barriers):
+// Structure (2.5D z-march).  A block owns a TX x TY column tile and a range of
+// z planes (a chunk of a (tile, chunk) grid, or the segments of a balanced
+// split, see the kernel).  It walks up the range with a ring of input planes in
+// shared memory over the tile plus a 2-cell halo (R2).  Thread i < TX*TY owns
+// tile column i; with WIDE the block has one thread per cell of the tile and
+// its four 1-cell edge strips (rounded up to whole warps), so the Eulerian
+// update of a plane is one item per thread.  Per plane e (two barriers):
 //   S0  asynchronous 8-byte copies of plane e+2 into a three-slot ring (the
 //       fields the faces need, + Phi), one full iteration ahead of its use;
 //   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
