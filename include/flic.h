@@ -109,14 +109,24 @@ typedef struct flic_diag {
 
 typedef struct flic_handle flic_handle;
 
-/* Allocates device state for one grid; *out receives the handle.  `stream` is a
+/* The grid and constants of Sec. 2: a uniform cubic grid of n^3 cells of width
+ * h = (box_max - box_min)/n, the adiabatic index gamma and the gravitational
+ * constant G of the equations of Sec. 2, the Courant number of the step size
+ * (Sec. 2 states no CFL formula; the library takes tau = courant * h / vmax with
+ * vmax as in flic_diag), the energy-balance switch eta of Sec. 2.4, and the
+ * Poisson boundary of Sec. 2.3 (periodic, as its discrete Fourier indices imply,
+ * or isolated).
+ * Allocates device state for one grid; *out receives the handle.  `stream` is a
  * cudaStream_t on which every launch of this handle is issued; NULL makes the
  * library create (and later destroy) a non-blocking stream of its own.  The
  * state starts as zeros; call flic_set_state first.  Errors: INVALID_ARG for an
  * unsupported n or constants, OOM / CUDA on allocation failures (nothing leaks). */
 int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out);
 
-/* Copies 22 host float64 arrays (field order above, N^3 each) to the device,
+/* The state of Sec. 2: the gas's conserved density, momentum, total and
+ * internal energy and the Boltzmann moments (density, momentum, energy tensor)
+ * with the velocity-dispersion tensor Pi of Sec. 2.2.
+ * Copies 22 host float64 arrays (field order above, N^3 each) to the device,
  * converting to the storage precision on the device, and computes the initial
  * signal speed.  Page-locked, device-mapped arrays (cudaHostAlloc) are read in
  * place by the conversion kernel; pageable arrays go through a staging copy.
@@ -134,13 +144,19 @@ int flic_get_state(flic_handle* h, double* const fields[FLIC_NFIELDS]);
 /* Same, into 22 device float64 arrays owned by the caller. */
 int flic_get_state_device(flic_handle* h, double* const fields[FLIC_NFIELDS]);
 
-/* One full step (Poisson, tau, both fluids, kappa, energy balance, diagnostics).
+/* One full time step of the method, Sec. 2.1-2.4: the potential of the total
+ * density (Sec. 2.3), the step size, the gas Eulerian stage with the face
+ * velocity and pressure of the linearised Riemann problem and the Lagrangian
+ * stage (Sec. 2.1), the Boltzmann-moment Eulerian stage with the closed-form face
+ * solution of its 6x6 system and the same Lagrangian stage (Sec. 2.2), then the
+ * kappa checks and the energy balance (Sec. 2.4), and the conserved sums.
+ * (Poisson, tau, both fluids, kappa, energy balance, diagnostics.)
  * dt > 0: fixed step; dt <= 0: CFL step tau = courant * h / vmax computed on the
  * device.  If dt_used is non-NULL the call waits for the step and stores tau;
  * otherwise it returns after enqueueing (stream-ordered). */
 int flic_step(flic_handle* h, double dt, double* dt_used);
 
-/* nsteps consecutive steps with no host synchronisation (CUDA-graph replay after
+/* nsteps consecutive steps of Sec. 2.1-2.4 (as flic_step) with no host synchronisation (CUDA-graph replay after
  * the first call for a given dt mode).  Waits for completion only if `sync`. */
 int flic_run(flic_handle* h, int nsteps, double dt, int sync);
 
@@ -160,11 +176,14 @@ int flic_launches_per_step(flic_handle* h);
  * to keep the potential on the device only. */
 int flic_solve_poisson(flic_handle* h, double* phi_out);
 
-/* Record of the last completed step (waits for the stream). */
+/* Record of the last completed step (waits for the stream): the kappa_gas and
+ * kappa_bme checks of Sec. 2.4 and the quantities whose conservation the paper
+ * reports for its cloud-collision test (Sec. 4.5: mass and total momentum kept
+ * by the scheme, the kinetic, internal and potential energies traced). */
 int flic_step_diagnostics(flic_handle* h, flic_diag* out);
 
-/* Diagnostics of the CURRENT state (solves Poisson for E_pot; kappa of the
- * current state; dt = 0). */
+/* The same quantities (Sec. 2.4; Sec. 4.5) for the CURRENT state (solves the
+ * Poisson equation of Sec. 2.3 for E_pot; kappa of the current state; dt = 0). */
 int flic_diagnostics(flic_handle* h, flic_diag* out);
 
 /* Diagnostics of a caller-owned float64 state with NO device allocation (no
@@ -182,18 +201,26 @@ int flic_diagnostics(flic_handle* h, flic_diag* out);
  * Scratch: the per-block partial sums live in one file-scope device array of
  * about 102 KiB (1024 partial rows) that every GPU loading the library keeps
  * until exit; n must be between 1 and 1024, larger grids are rejected with
- * FLIC_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (with that device current); make that first call before any
- * stream capture.  Every call shares the array and leaves the last call's
- * contents in it; the scalars that must start at zero are cleared on entry.
- * Calls that overlap on the GPU (different streams or threads) race on it.
- * Runs on `stream` (cudaStream_t, NULL = legacy default stream) and waits for
- * it.  Errors: INVALID_ARG, CUDA (message in flic_last_error(NULL)),
- * NONPHYSICAL (record still written). */
+ * FLIC_ERR_INVALID_ARG.  The array belongs to the library's device code, which
+ * the CUDA runtime loads onto a device at the first call of this library there
+ * (this call or any other), so that first call needs the device memory for it.
+ * The first call of this entry point on a device looks up the array's device
+ * address (with that device current) and keeps it for the process; make that
+ * first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) while the library is in use.  Every call shares the array
+ * and leaves the last call's contents in it; the scalars that must start at
+ * zero are cleared on entry.  Calls that overlap on the GPU (different streams
+ * or threads) race on it.  The call is synchronous: it runs on `stream`
+ * (cudaStream_t, NULL = legacy default stream), waits for that stream and copies
+ * the record to *out before it returns.  Errors: INVALID_ARG, CUDA (message in
+ * flic_last_error(NULL)), NONPHYSICAL (record still written). */
 int flic_state_diagnostics_noalloc(const double* const fields[FLIC_NFIELDS], const double* phi, int n, double h,
                                    double gamma, void* stream, flic_diag* out);
 
 /* ---- batched ensembles (independent runs, uneven sizes, advanced together) ----
+ *
+ * A deployment form of the step of Sec. 2.1-2.4 with no counterpart in the
+ * paper: each run takes exactly the steps flic_step would take on its own grid.
  *
  * nruns grids, descs[r] for run r; every constant except n must be equal across
  * runs (n = 2^a 3^b, multiple of 4, 8..512).  Each step solves every run's
@@ -221,7 +248,7 @@ int flic_ensemble_launches_per_step(flic_ensemble* e);
 int flic_ensemble_destroy(flic_ensemble* e);
 const char* flic_ensemble_last_error(flic_ensemble* e);
 
-/* Waits for all work of the handle. */
+/* Waits for all work of the handle (no counterpart in the paper). */
 int flic_sync(flic_handle* h);
 
 int flic_destroy(flic_handle* h);

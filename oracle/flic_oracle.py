@@ -238,18 +238,28 @@ def _crop(a, m):
     return a[..., m:-m, m:-m, m:-m]
 
 
-def advance(st, phi, tau, prm: Params):
+def advance(st, phi, tau, prm: Params, record=None):
     """Eulerian stage, Lagrangian stage and energy balance of both fluids.
 
     Returns ``(new_state, kappa)`` where ``kappa`` holds the per-cell integrands of
     kappa_gas and kappa_bme (Sec. 2.4, times h^3) measured on the post-Lagrangian
     state before the balance.
+
+    ``record``: an optional dict that receives, per cell, which branch of the
+    energy balance (reading s11) was taken and how far from its switch the cell
+    was (instrumentation for tests; the arithmetic is unchanged):
+    ``gas_take`` (e = E - K taken), ``gas_margin`` ((E - K - eta E) / |E|),
+    ``bme_take`` (Pi = nE - q q^T/n taken), ``bme_trace_margin``
+    ((tr Pi^E - eta tr nE) / |tr nE|), ``bme_diag_min`` (min_d Pi^E_dd / |tr nE|).
     """
     if prm.boundary == "outflow":
         # reading s8: the update of a cell reaches 2 cells, so 2 ghost layers
         # make the periodic shifts below act as the zero-gradient boundary
         ext = {f: _extend(st[f], 2) for f in FIELDS}
-        new, kap = advance(ext, _extend(phi, 2), tau, replace(prm, boundary="periodic"))
+        rec = {} if record is not None else None
+        new, kap = advance(ext, _extend(phi, 2), tau, replace(prm, boundary="periodic"), rec)
+        if record is not None:
+            record.update({k: _crop(v, 2) for k, v in rec.items()})
         return {f: _crop(new[f], 2) for f in FIELDS}, {k: _crop(v, 2) for k, v in kap.items()}
     if prm.boundary != "periodic":
         raise ValueError(prm.boundary)
@@ -325,6 +335,9 @@ def advance(st, phi, tau, prm: Params):
     kap_gas = np.abs(new["E"] - new["e"] - K) * vol
     epsE = new["E"] - K
     take = epsE >= eta * new["E"]
+    if record is not None:
+        record["gas_take"] = take
+        record["gas_margin"] = (epsE - eta * new["E"]) / np.abs(new["E"])
     e2 = np.where(take, epsE, new["e"])
     E2 = np.where(take, new["E"], new["e"] + K)
     new["e"], new["E"] = e2, E2
@@ -336,6 +349,10 @@ def advance(st, phi, tau, prm: Params):
     tr_PiE = PiE["xx"] + PiE["yy"] + PiE["zz"]
     tr_nE = new["nExx"] + new["nEyy"] + new["nEzz"]
     take = (tr_PiE >= eta * tr_nE) & (PiE["xx"] > 0.0) & (PiE["yy"] > 0.0) & (PiE["zz"] > 0.0)
+    if record is not None:
+        record["bme_take"] = take
+        record["bme_trace_margin"] = (tr_PiE - eta * tr_nE) / np.abs(tr_nE)
+        record["bme_diag_min"] = np.minimum(np.minimum(PiE["xx"], PiE["yy"]), PiE["zz"]) / np.abs(tr_nE)
     for k in nE:
         Pk = np.where(take, PiE[k], new["P" + k])
         nEk = np.where(take, new["nE" + k], new["P" + k] + qq[k])

@@ -425,6 +425,21 @@ struct Geom {
         16 * 16;
     static constexpr size_t tab_offset = red_offset + sizeof(double) * 32 * (P::NQ + 1);
     static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (2 * CPR + H2);
+
+    // Alignment of every 8-byte shared-memory access (the asynchronous copies,
+    // float2 field pairs, double partials).  The copies land at ring + slot * NR
+    // * R2 + r * R2 + row * W2 + chunk * CH and exb + (slot * NEX + k) * H1 * W2 +
+    // row * W2 + chunk * CH; all terms are multiples of CH when W2 is, and the
+    // region bases must be too.  Global sources are x0 - 2 + CH * i (x0 a multiple
+    // of TX) plus multiples of N (a multiple of 4) and of the field stride (a
+    // multiple of 64), so TX must be a multiple of CH.
+    static_assert(TX % CH == 0, "tile columns must start on an 8-byte boundary");
+    static_assert((size_t(RING_SLOTS) * P::NR * R2) % CH == 0 && R2 % CH == 0, "ring slots and fields 8-byte aligned");
+    static_assert(!SEX || ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems) * sizeof(T)) % 8 == 0,
+                  "staged energy-tensor rows must start on an 8-byte boundary");
+    static_assert(!SEX || (size_t(Geom::H1) * W2) % CH == 0, "staged energy-tensor fields 8-byte aligned");
+    static_assert(red_offset % 16 == 0 && tab_offset % 8 == 0, "reduction scratch and tables aligned");
+    static_assert(smem_bytes <= 227 * 1024, "shared memory of one block");
 };
 
 // Updated cell i -> R1 coordinates (jx, jy): tile cells first (so that thread i

@@ -101,3 +101,58 @@ def reflect_x(st):
         odd = f in ("mx", "qx") or f in ("nExy", "nExz", "Pxy", "Pxz")
         out[f] = np.ascontiguousarray(-a if odd else a)
     return out
+
+
+def balance_branch_state(N, seed, gamma=5.0 / 3.0):
+    """A rough random N^3 state whose cells, after one step, fall clearly on
+    either side of the energy balance's switches (reading s11), in a pattern that
+    makes neighbouring cells take different branches.
+
+    Gas: consistent cells (E = e + K, so E - K = e >> eta E: e is taken from E)
+    next to cells with E = K - e/2 (E - K < 0: E is reset from e).  Moments,
+    cycling over four cell classes: consistent (nE = Pi + q q^T/n), a negative
+    diagonal of Pi^E = nE - q q^T/n along x (Pi^E_xx = -Pi_xx, with the other
+    two diagonal entries raised to 3 Pi_dd so the trace stays positive), the same
+    along z, and a negative trace of Pi^E; all but the first are reset.
+    """
+    from paper_1311_0861_gb300.inputs import random_state
+
+    s = random_state((N, N, N), seed=seed, rough=True)
+    st = {f: v.copy() for f, v in s.state.items()}
+    k, j, i = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    K = (st["mx"] ** 2 + st["my"] ** 2 + st["mz"] ** 2) / (2.0 * st["rho"])
+    odd = (i + j + k) % 2 == 1
+    st["E"] = np.where(odd, K - 0.5 * st["e"], st["e"] + K)
+    cls = (i + 2 * j + 3 * k) % 4
+    q = {"x": st["qx"], "y": st["qy"], "z": st["qz"]}
+    for c in TENSOR:
+        qq = q[c[0]] * q[c[1]] / st["n"]
+        P = st["P" + c]
+        dev = np.zeros_like(P)
+        if c[0] == c[1]:
+            dev = np.where(cls == 1, (-2.0 if c == "xx" else 2.0) * P, dev)
+            dev = np.where(cls == 2, (-2.0 if c == "zz" else 2.0) * P, dev)
+            dev = np.where(cls == 3, -2.0 * P, dev)
+        st["nE" + c] = qq + P + dev
+    return s.__class__(st, s.h, gamma)
+
+
+def cold_flow_state(N, mach, gamma=5.0 / 3.0):
+    """A cold, fast N^3 flow on [-1, 1]^3: both fluids stream along x at 0.5
+    (the moments at 0.4 along x and 0.1 along y) with a weak shear and a 10 %
+    density ripple; the gas sound speed and the moments' dispersion speed
+    sqrt(3 Pi_dd / n) are 0.5 / mach, so the kinetic energy exceeds the thermal
+    one by about mach^2 and E - |m|^2/(2 rho) is a small difference of large
+    numbers."""
+    h = 2.0 / N
+    c = -1.0 + (np.arange(N) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rho = 1.0 + 0.1 * np.sin(np.pi * x) * np.cos(np.pi * y)
+    cs = 0.5 / mach
+    p = rho * cs * cs / gamma
+    v = (0.5 + 0.02 * np.sin(np.pi * y), 0.02 * np.cos(np.pi * z), 0.0 * rho)
+    n = 0.5 * (1.0 + 0.1 * np.cos(np.pi * (x + z)))
+    u = (0.4 + 0.02 * np.sin(np.pi * z), 0.1 + 0.0 * n, 0.02 * np.sin(np.pi * x))
+    s2 = cs * cs / 3.0
+    P = {k: (n * s2 if k[0] == k[1] else 0.0 * n) for k in TENSOR}
+    return state_from_primitives(rho, v, p, n, u, P, gamma), h
