@@ -152,37 +152,67 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_sample(setup, budget_s: float):
-    """Times the FP64 oracle on a bounded slab of the workload.
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
-    The Poisson solve of the whole grid is timed once; the Eulerian/Lagrangian/
-    balance update is timed on a slab of S z-planes (S sized to ``budget_s``).
-    The full-step time is estimated as t_poisson + N * t_slab / S and the rate
-    as N^3 over that estimate."""
+
+def oracle_full_steps(setup, nsteps: int, warmup: int = 0, workers=None):
+    """Times full oracle steps of the whole grid on the host cores.
+
+    Each step is the oracle's own step (whole-grid Poisson solve and CFL step,
+    then the update slab by slab over ``workers`` processes, default all host
+    cores: ``oracle.slab_pool``).  Returns per-step seconds and the worker count."""
+    import oracle as O
+    from oracle.slab_pool import SlabPool
+    prm = O.Params(h=setup.h, gamma=setup.gamma)
+    with SlabPool(setup.shape, workers=workers) as pool:
+        pool.load(setup.state)
+        for _ in range(warmup):
+            pool.step(prm)
+        secs = []
+        for _ in range(nsteps):
+            t = time.perf_counter()
+            pool.step(prm)
+            secs.append(time.perf_counter() - t)
+        return secs, pool.workers
+
+
+def oracle_one_core_sample(setup, budget_s: float):
+    """The oracle on one core, on a bounded sample: the whole-grid Poisson solve
+    and CFL step, plus the update of a slab of S z-planes (S sized to
+    ``budget_s``), scaled to the full grid as t_poisson + t_cfl + N t_slab / S."""
     import oracle as O
     st = setup.state
     N = setup.shape[0]
     prm = O.Params(h=setup.h, gamma=setup.gamma)
     t = time.perf_counter()
     phi = O.solve_poisson(st, prm)
-    t_poisson = time.perf_counter() - t
     tau = O.cfl_dt(st, prm)
+    t_serial = time.perf_counter() - t
     t = time.perf_counter()
-    O.advance_window(st, phi, tau, prm, zslab=(0, 1))
-    t_plane = time.perf_counter() - t
-    S = int(max(1, min(N, (budget_s - t_poisson) / max(t_plane, 1e-6))))
+    O.advance_window(st, phi, tau, prm, zslab=(0, 2))
+    t_plane = (time.perf_counter() - t) / 2
+    S = int(max(2, min(N, (budget_s - t_serial) / max(t_plane, 1e-6))))
     t = time.perf_counter()
     O.advance_window(st, phi, tau, prm, zslab=(N // 2, N // 2 + S))
     t_slab = time.perf_counter() - t
-    est = t_poisson + N * t_slab / S
-    return {"value": N ** 3 / est, "seconds_per_step_estimate": est, "planes": S,
-            "t_poisson": t_poisson, "t_slab": t_slab}
-
-
-def cpu_cores_used():
-    """Threads the oracle runs on: its numpy element-wise operations and numpy's
-    FFT are single-threaded (no BLAS call is on its path), so one core."""
-    return 1
+    est = t_serial + N * t_slab / S
+    return {"value": N ** 3 / est, "seconds_per_step_estimate": est, "planes": S}
 
 
 def reference_arm(args):
@@ -191,27 +221,21 @@ def reference_arm(args):
         return 0
     from paper_1311_0861_gb300 import inputs
     setup = inputs.head_on(args.n)
-    # per-step budget so that warm-up + timed steps end within ~2 minutes
-    budget = max(0.5, 120.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_sample(setup, budget)
-    vals, secs, planes = [], [], []
-    for _ in range(args.steps):
-        r = oracle_sample(setup, budget)
-        vals.append(r["value"])
-        secs.append(r["seconds_per_step_estimate"])
-        planes.append(r["planes"])
-    value = float(np.median(vals))
-    cores = cpu_cores_used()
-    sample = (f"oracle (numpy FP64) on the {args.n}^3 head-on collision: whole-grid Poisson solve + "
-              f"update of a slab of {int(np.median(planes))} z-planes per step, scaled to the full grid")
+    # every step is a full oracle step of the whole grid on all host cores
+    secs, workers = oracle_full_steps(setup, args.steps, warmup=args.warmup)
+    total = float(np.sum(secs))
+    value = args.n ** 3 * args.steps / total
+    sample = (f"oracle (numpy FP64) on the {args.n}^3 head-on collision: {args.steps} full steps timed after "
+              f"{args.warmup} untimed ones; each step is the whole-grid Poisson solve and CFL step in one process "
+              f"and the update in z-slabs over {workers} worker processes; CPU: {cpu_model()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(secs)),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"head-on two-galaxy collision {args.n}^3", "n": args.n,
                        "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -276,6 +300,8 @@ def run_single(args, rank, world, stream, clocks):
     esz = 4 if args.precision == "mixed" else 8
     g = flic.Grid(N, precision=args.precision, gamma=setup.gamma, poisson=poisson, stream=stream.cuda_stream)
     g.set_state(setup.state)
+    tune = g.autotune(reps=5)
+    tiles = g.tile_config()["text"]
     launches = g.launches_per_step()
     clocks.start()
     time.sleep(0.2)
@@ -333,6 +359,7 @@ def run_single(args, rank, world, stream, clocks):
         g.close()
         g64 = flic.Grid(N, precision="fp64", gamma=setup.gamma, poisson=poisson, stream=stream.cuda_stream)
         g64.set_state(setup.state)
+        g64.autotune(reps=2)
         g64.run(2, sync=True)
         st64, tot64 = g64.profile(args.fp64_steps)
         v64 = N ** 3 * args.fp64_steps / (tot64 / 1e3)
@@ -340,8 +367,7 @@ def run_single(args, rank, world, stream, clocks):
         g64.run(10, sync=True)
         fp6410 = g64.get_state()
         g64.close()
-        l1 = {f: float(np.sum(np.abs(mixed10[f] - fp6410[f])) / np.sum(np.abs(fp6410[f])))
-              for f in ("rho", "n", "E", "e", "Pxx")}
+        l1 = {f: float(np.sum(np.abs(mixed10[f] - fp6410[f])) / np.sum(np.abs(fp6410[f]))) for f in flic.FIELDS}
         compare = {"fp64_value": v64 * world, "fp64_ms_per_step": tot64 / args.fp64_steps,
                    "mixed_over_fp64": value / (v64 * world),
                    "rel_l1_mixed_vs_fp64_after_10_steps": l1}
@@ -350,13 +376,23 @@ def run_single(args, rank, world, stream, clocks):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and poisson == "periodic":
-        r = oracle_sample(setup, 20.0)
-        cpu = {"value": r["value"], "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": (f"numpy FP64 oracle: whole-grid Poisson solve ({r['t_poisson']:.1f} s) + update of "
-                          f"{r['planes']} of {N} z-planes ({r['t_slab']:.1f} s), scaled to one full step")}
+        # two full oracle steps of the whole grid on all host cores (bounded: a
+        # few seconds each at 256^3), and a one-core sample scaled to a step
+        secs, workers = oracle_full_steps(setup, 2)
+        one = oracle_one_core_sample(setup, 10.0)
+        cpu = {"value": N ** 3 * len(secs) / float(np.sum(secs)), "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": (f"numpy FP64 oracle: {len(secs)} full {N}^3 steps (whole-grid Poisson solve and CFL "
+                          f"step, then the update in z-slabs over {workers} worker processes), "
+                          f"{float(np.mean(secs)):.2f} s per step"),
+               "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+               "one_core": {"value": one["value"], "cores": 1,
+                            "sample": (f"whole-grid Poisson solve and CFL step + update of {one['planes']} of {N} "
+                                       f"z-planes on one core, scaled to one full step")}}
     line = {"value": value, "ms_per_step": agg["max_s"] * 1e3 / args.steps,
             "config": {"workload": name, "n": N, "precision": args.precision,
-                       "poisson": f"{poisson} FFT",
+                       "poisson": f"{poisson} FFT", "tiles": tiles,
+                       "tiles_chosen_by": "cached launch-shape tuner" if tune["cached"] else
+                       "launch-shape tuner (every compiled shape timed on this GPU)",
                        "l2": f"inputs larger than L2 (state {22 * esz * N ** 3 / 2 ** 30:.2f} GiB)"
                        if 22 * esz * N ** 3 > 2 ** 27 else "state smaller than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -378,6 +414,8 @@ def run_ensemble(args, rank, world, stream, clocks):
     ens = flic.Ensemble(sizes, precision=args.precision, stream=stream.cuda_stream)
     for r, m in enumerate(members):
         ens.set_state(r, m.state)
+    ens.autotune(reps=2)
+    tiles = ens.tile_config()["text"]
     launches = ens.launches_per_step()
     clocks.start()
     time.sleep(0.2)
@@ -405,6 +443,7 @@ def run_ensemble(args, rank, world, stream, clocks):
     for m in members:
         with flic.Grid(m.shape[0], precision=args.precision, gamma=m.gamma, stream=stream.cuda_stream) as g:
             g.set_state(m.state)
+            g.autotune(reps=2)
             g.run(2, sync=True)
             _, tot = g.profile(seq_steps)
             seq_ms += tot
@@ -441,6 +480,8 @@ def run_ensemble(args, rank, world, stream, clocks):
             "config": {"workload": "64-run collision ensemble, uneven grids " +
                        ", ".join(f"{c}x{n}^3" for n, c in counts.items()),
                        "cells_per_step": cells, "precision": args.precision, "poisson": "periodic FFT",
+                       "tiles": tiles, "tiles_chosen_by": "launch-shape tuner (every compiled shape and chunk cap "
+                                                         "timed over the ensemble's work list on this GPU)",
                        "l2": f"state {22 * esz * cells / 2 ** 30:.2f} GiB",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": None, "e2e": e2e,

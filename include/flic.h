@@ -172,6 +172,39 @@ int flic_profile(flic_handle* h, int nsteps, double dt, double stage_ms[FLIC_NST
 /* Number of kernels one step launches (for launch accounting). */
 int flic_launches_per_step(flic_handle* h);
 
+/* ---- launch-shape tuner (no counterpart in the paper) ----
+ *
+ * Each fluid kernel (gas: Sec. 2.1, 2.4; moments: Sec. 2.2, 2.4) is compiled in
+ * several launch shapes -- tile of columns, threads per block, blocks per SM --
+ * each used with a z split over blocks (a balanced split over one block per
+ * resident slot, or z chunks); which is fastest depends on the GPU and the grid
+ * size, not on the method.  The shapes compute the same cell updates; only the
+ * partial sums of the diagnostics are grouped differently.
+ *
+ * flic_autotune times every shape of both kernels on the handle's CURRENT state
+ * (call it after flic_set_state): one untimed launch, then `reps` launches
+ * between two CUDA events on the handle's stream, and keeps the fastest shape of
+ * each kernel.  The launches write only the library's spare state buffer: the
+ * current state, time, step count and CFL signal speed are unchanged.  With
+ * use_cache != 0 a choice made earlier in this process for the same device model,
+ * n, precision and hydro boundary is applied without timing (return value 1);
+ * otherwise the shapes are timed and the choice is cached (return value 0).
+ * ms (nullable) receives, when timing, the mean milliseconds per launch of every
+ * shape (gas shapes first, then moment shapes; -1 for a shape the device cannot
+ * launch).  Errors: INVALID_ARG (reps < 1), CUDA. */
+int flic_autotune(flic_handle* h, int reps, int use_cache, double* ms);
+
+/* Number of compiled shapes of the gas and moment kernels for this handle's precision. */
+int flic_num_tile_configs(flic_handle* h, int* n_gas, int* n_bme);
+
+/* Selects shape `gas` / `bme` (indices below flic_num_tile_configs; -1 keeps the
+ * current one).  Shape 0 of each kernel is the default of a new handle. */
+int flic_set_tile_config(flic_handle* h, int gas, int bme);
+
+/* The shapes in use: their indices (nullable pointers) and, when text is not
+ * NULL, a description of at most len - 1 characters. */
+int flic_tile_config(flic_handle* h, int* gas, int* bme, char* text, int len);
+
 /* Solves Sec. 2.3 for the current state; phi_out (host, N^3 float64) may be NULL
  * to keep the potential on the device only. */
 int flic_solve_poisson(flic_handle* h, double* phi_out);
@@ -245,6 +278,21 @@ int flic_ensemble_diagnostics(flic_ensemble* e, int run, flic_diag* out);
 int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double stage_ms[FLIC_NSTAGES],
                           double* total_ms);
 int flic_ensemble_launches_per_step(flic_ensemble* e);
+/* Launch-shape tuner of an ensemble (see flic_autotune): every compiled shape of
+ * each fluid kernel is timed over the whole work list with work items of at most
+ * 16, 32 and 64 z planes (`reps` launches after one untimed launch, on the
+ * current states; only the spare state buffers are written), and the fastest
+ * (shape, chunk height) of each kernel is kept.  ms (nullable) receives 3 values
+ * per shape (gas shapes first; -1 for a shape that is skipped, i.e. one that
+ * differs from an earlier entry only in its single-grid split, or that the
+ * device cannot launch).  No caching. */
+int flic_ensemble_autotune(flic_ensemble* e, int reps, double* ms);
+/* Number of compiled shapes of the gas and moment kernels for this ensemble's precision. */
+int flic_ensemble_num_tile_configs(flic_ensemble* e, int* n_gas, int* n_bme);
+/* Selects the shapes and the z-chunk caps of the work items (-1 keeps the current value). */
+int flic_ensemble_set_tile_config(flic_ensemble* e, int gas, int bme, int tz_gas, int tz_bme);
+/* The shapes and chunk caps in use (nullable pointers) and their description. */
+int flic_ensemble_tile_config(flic_ensemble* e, int* gas, int* bme, int* tz_gas, int* tz_bme, char* text, int len);
 int flic_ensemble_destroy(flic_ensemble* e);
 const char* flic_ensemble_last_error(flic_ensemble* e);
 

@@ -11,7 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflic.so")
-SOURCES = ["flic_api.cu", "flic_stencil.cu", "flic_fft.cu", "flic_fft_iso.cu", "flic_util.cu", "flic_noalloc.cu", "flic_ensemble.cu"]
+SOURCES = ["flic_api.cu", "flic_stencil.cu", "flic_stencil_gas32.cu", "flic_stencil_bme32.cu", "flic_stencil_gas64.cu",
+           "flic_stencil_bme64.cu", "flic_fft.cu", "flic_fft_iso.cu", "flic_util.cu", "flic_noalloc.cu",
+           "flic_ensemble.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xptxas", "-v"]
@@ -27,7 +29,8 @@ def nvcc() -> str:
 # float32 denormals flush to zero in the stencil kernels (state magnitudes are
 # far from the denormal range; saves the special-case paths of the hardware
 # reciprocal and reciprocal square root)
-EXTRA = {"flic_stencil.cu": ["-ftz=true"]}
+EXTRA = {src: ["-ftz=true"] for src in ("flic_stencil_gas32.cu", "flic_stencil_bme32.cu",
+                                         "flic_stencil_gas64.cu", "flic_stencil_bme64.cu")}
 
 
 def _compile(src: str) -> tuple[str, str]:

@@ -3,7 +3,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "flic_fft.h"
 #include "flic_internal.h"
@@ -37,6 +40,7 @@ struct flic_handle {
     double* level1 = nullptr;         // second-level partial sums
     int nb_diag = 0;
     StepCfg gcfg, bcfg;
+    int rows_gas = 0, rows_bme = 0;   // partial rows allocated per fluid kernel
     flic_diag* diag_dev = nullptr;    // [0] last step, [1] current-state diagnostics
     flic_diag* diag_host = nullptr;   // pinned
     double* staging = nullptr;        // one float64 field
@@ -88,16 +92,10 @@ static int enqueue_poisson(flic_handle* h) {
     return FLIC_OK;
 }
 
-// One full step on the handle's stream; flips the state buffers.  With `ev`
-// (5 events) the stage boundaries are recorded: start, after the Poisson solve,
-// after the gas kernel, after the moment kernel, after the final reduction.
+// Arguments of one fluid kernel of the current step (state[cur] -> state[1 - cur])
+// launched with geometry c.
 template <typename T>
-static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
-    if (ev) FLIC_CK(h, cudaEventRecord(ev[0], h->st));
-    FLIC_CK(h, step_prep(h->scal, h->status, dt, h->d.courant * h->h, h->st));
-    int rc = enqueue_poisson<T>(h);
-    if (rc) return rc;
-    if (ev) FLIC_CK(h, cudaEventRecord(ev[1], h->st));
+static StencilArgs<T> fluid_args(const flic_handle* h, int fluid, const StepCfg& c) {
     StencilArgs<T> a;
     a.phi = reinterpret_cast<const T*>(h->phi);
     a.fs = h->fs;
@@ -109,23 +107,31 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
     a.eta = T(h->d.eta);
     a.vmax = h->scal + S_VMAX_NEXT;
     a.status = h->status;
-    // gas: fields 0..5
-    a.in = field_ptr<T>(h->state[h->cur], h->fs, F_RHO);
-    a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, F_RHO);
-    a.tz = h->gcfg.tz;
-    a.tiles_x = h->gcfg.tiles_x;
-    a.tiles_y = h->gcfg.tiles_y;
-    a.partials = h->part_gas;
-    FLIC_CK(h, launch_gas<T>(a, h->gcfg, h->st));
+    const int f0 = fluid == FLUID_GAS ? F_RHO : F_N;   // gas: fields 0..5; moments: 6..21
+    a.in = field_ptr<T>(h->state[h->cur], h->fs, f0);
+    a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, f0);
+    a.tz = c.tz;
+    a.tiles_x = c.tiles_x;
+    a.tiles_y = c.tiles_y;
+    a.partials = fluid == FLUID_GAS ? h->part_gas : h->part_bme;
+    return a;
+}
+
+// One full step on the handle's stream; flips the state buffers.  With `ev`
+// (5 events) the stage boundaries are recorded: start, after the Poisson solve,
+// after the gas kernel, after the moment kernel, after the final reduction.
+template <typename T>
+static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[0], h->st));
+    FLIC_CK(h, step_prep(h->scal, h->status, dt, h->d.courant * h->h, h->st));
+    int rc = enqueue_poisson<T>(h);
+    if (rc) return rc;
+    if (ev) FLIC_CK(h, cudaEventRecord(ev[1], h->st));
+    const StencilArgs<T> ag = fluid_args<T>(h, FLUID_GAS, h->gcfg);
+    FLIC_CK(h, stencil_launch<T>(FLUID_GAS, ag, h->gcfg, h->st));
     if (ev) FLIC_CK(h, cudaEventRecord(ev[2], h->st));
-    // moments: fields 6..21
-    a.in = field_ptr<T>(h->state[h->cur], h->fs, F_N);
-    a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, F_N);
-    a.tz = h->bcfg.tz;
-    a.tiles_x = h->bcfg.tiles_x;
-    a.tiles_y = h->bcfg.tiles_y;
-    a.partials = h->part_bme;
-    FLIC_CK(h, launch_bme<T>(a, h->bcfg, h->st));
+    const StencilArgs<T> ab = fluid_args<T>(h, FLUID_BME, h->bcfg);
+    FLIC_CK(h, stencil_launch<T>(FLUID_BME, ab, h->bcfg, h->st));
     if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));
     FLIC_CK(h, step_finalize(h->part_gas, h->gcfg.num_blocks(), h->part_bme, h->bcfg.num_blocks(),
                              h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
@@ -225,8 +231,18 @@ static int init_impl(flic_handle* h) {
     FLIC_CK(h, stencil_prepare<T>());
     FLIC_CK(h, fft_prepare<T>(N));
     if (h->iso) FLIC_CK(h, fft_prepare_iso<T>(N));
-    h->gcfg = gas_cfg<T>(N, 0);
-    h->bcfg = bme_cfg<T>(N, 0);
+    h->gcfg = stencil_cfg<T>(FLUID_GAS, 0, N, 0);
+    h->bcfg = stencil_cfg<T>(FLUID_BME, 0, N, 0);
+    // partial rows for the largest grid of any candidate shape (the tuner may switch)
+    for (int fluid = 0; fluid < 2; ++fluid) {
+        int nc = 0;
+        stencil_cands<T>(fluid, &nc);
+        for (int c = 0; c < nc; ++c) {
+            const int nb = stencil_cfg<T>(fluid, c, N, 0).num_blocks();
+            int& m = fluid == FLUID_GAS ? h->rows_gas : h->rows_bme;
+            if (nb > m) m = nb;
+        }
+    }
     h->nb_diag = 152 * 4;
     for (int i = 0; i < 2; ++i) {
         FLIC_CK(h, cudaMalloc(&h->state[i], F_COUNT * h->fs * sizeof(T)));
@@ -277,7 +293,7 @@ static int init_impl(flic_handle* h) {
     FLIC_CK(h, cudaMemsetAsync(h->scal, 0, S_COUNT * sizeof(double), h->st));
     FLIC_CK(h, cudaMalloc(&h->status, sizeof(unsigned int)));
     FLIC_CK(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->st));
-    const size_t pg = size_t(h->gcfg.num_blocks()) * Q_COUNT, pb = size_t(h->bcfg.num_blocks()) * Q_COUNT;
+    const size_t pg = size_t(h->rows_gas) * Q_COUNT, pb = size_t(h->rows_bme) * Q_COUNT;
     FLIC_CK(h, cudaMalloc(&h->part_gas, pg * sizeof(double)));
     FLIC_CK(h, cudaMalloc(&h->part_bme, pb * sizeof(double)));
     FLIC_CK(h, cudaMalloc(&h->part_diag, size_t(h->nb_diag) * Q_COUNT * sizeof(double)));
@@ -290,6 +306,104 @@ static int init_impl(flic_handle* h) {
     FLIC_CK(h, cudaMalloc(&h->staging, h->cells * sizeof(double)));
     FLIC_CK(h, cudaStreamSynchronize(h->st));
     return FLIC_OK;
+}
+
+// ---- launch-shape tuner ------------------------------------------------------
+// Choices made in this process, per (device name and SM count, n, precision,
+// hydro boundary): (gas candidate, moment candidate).
+typedef std::tuple<std::string, int, int, int> TuneKey;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+static TuneKey tune_key(const flic_handle* h) {
+    int dev = 0;
+    cudaDeviceProp p;
+    std::string name = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&p, dev) == cudaSuccess)
+        name = std::string(p.name) + "/" + std::to_string(p.multiProcessorCount);
+    return TuneKey(name, h->N, h->d.precision, h->d.hydro_bc);
+}
+
+static void drop_graphs(flic_handle* h) {
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) {
+            cudaGraphExecDestroy(h->graph[i]);
+            h->graph[i] = nullptr;
+        }
+}
+
+template <typename T>
+static int apply_tile_config(flic_handle* h, int gas, int bme) {
+    int ng = 0, nb = 0;
+    stencil_cands<T>(FLUID_GAS, &ng);
+    stencil_cands<T>(FLUID_BME, &nb);
+    if (gas >= ng || bme >= nb || gas < -1 || bme < -1) {
+        h->err = "launch shape index out of range";
+        return FLIC_ERR_INVALID_ARG;
+    }
+    FLIC_CK(h, cudaStreamSynchronize(h->st));
+    if (gas >= 0) h->gcfg = stencil_cfg<T>(FLUID_GAS, gas, h->N, 0);
+    if (bme >= 0) h->bcfg = stencil_cfg<T>(FLUID_BME, bme, h->N, 0);
+    drop_graphs(h);
+    return FLIC_OK;
+}
+
+// Times every candidate shape of both fluid kernels on the current state (one
+// untimed launch, then `reps` launches between two events) and applies the
+// fastest.  The launches write the spare state buffer only, so the current
+// state, the step count and the CFL signal speed are unchanged.
+template <typename T>
+static int tune_impl(flic_handle* h, int reps, double* ms) {
+    FLIC_CK(h, step_prep(h->scal, h->status, 0.0, h->d.courant * h->h, h->st));
+    int rc = enqueue_poisson<T>(h);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FLIC_CK(h, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        FLIC_CK(h, ce);
+    }
+    int best[2] = {0, 0};
+    int k = 0;
+    for (int fluid = 0; fluid < 2 && rc == FLIC_OK; ++fluid) {
+        int nc = 0;
+        stencil_cands<T>(fluid, &nc);
+        double best_ms = -1.0;
+        for (int c = 0; c < nc; ++c, ++k) {
+            const StepCfg cfg = stencil_cfg<T>(fluid, c, h->N, 0);
+            const StencilArgs<T> a = fluid_args<T>(h, fluid, cfg);
+            double t = -1.0;
+            if (cfg.num_blocks() <= (fluid == FLUID_GAS ? h->rows_gas : h->rows_bme)) {
+                cudaError_t e = stencil_launch<T>(fluid, a, cfg, h->st);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, h->st);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = stencil_launch<T>(fluid, a, cfg, h->st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, h->st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float el = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
+                if (e == cudaSuccess) {
+                    t = double(el) / reps;
+                } else if (e == cudaErrorInvalidConfiguration || e == cudaErrorLaunchOutOfResources ||
+                           e == cudaErrorInvalidValue) {
+                    cudaGetLastError();   // a shape this device cannot launch: skipped
+                } else {
+                    h->err = std::string("launch-shape tuning: ") + cudaGetErrorString(e);
+                    rc = FLIC_ERR_CUDA;
+                    break;
+                }
+            }
+            if (ms) ms[k] = t;
+            if (t >= 0.0 && (best_ms < 0.0 || t < best_ms)) {
+                best_ms = t;
+                best[fluid] = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    return apply_tile_config<T>(h, best[0], best[1]);
 }
 
 extern "C" {
@@ -477,6 +591,65 @@ int flic_diagnostics(flic_handle* h, flic_diag* out) {
     return FLIC_OK;
 }
 
+int flic_num_tile_configs(flic_handle* h, int* n_gas, int* n_bme) {
+    if (!h || !n_gas || !n_bme) return FLIC_ERR_INVALID_ARG;
+    if (h->fp64) {
+        stencil_cands<double>(FLUID_GAS, n_gas);
+        stencil_cands<double>(FLUID_BME, n_bme);
+    } else {
+        stencil_cands<float>(FLUID_GAS, n_gas);
+        stencil_cands<float>(FLUID_BME, n_bme);
+    }
+    return FLIC_OK;
+}
+
+int flic_set_tile_config(flic_handle* h, int gas, int bme) {
+    if (!h) return FLIC_ERR_INVALID_ARG;
+    return h->fp64 ? apply_tile_config<double>(h, gas, bme) : apply_tile_config<float>(h, gas, bme);
+}
+
+int flic_tile_config(flic_handle* h, int* gas, int* bme, char* text, int len) {
+    if (!h) return FLIC_ERR_INVALID_ARG;
+    if (gas) *gas = h->gcfg.cand;
+    if (bme) *bme = h->bcfg.cand;
+    if (text && len > 0) {
+        int ng = 0, nb = 0;
+        const char* gn = h->fp64 ? stencil_cands<double>(FLUID_GAS, &ng)[h->gcfg.cand].name
+                                 : stencil_cands<float>(FLUID_GAS, &ng)[h->gcfg.cand].name;
+        const char* bn = h->fp64 ? stencil_cands<double>(FLUID_BME, &nb)[h->bcfg.cand].name
+                                 : stencil_cands<float>(FLUID_BME, &nb)[h->bcfg.cand].name;
+        char gs[64], bs[64];
+        if (h->gcfg.balanced > 0) snprintf(gs, sizeof gs, "balanced split over %d blocks", h->gcfg.balanced);
+        else snprintf(gs, sizeof gs, "z chunks of %d planes", h->gcfg.tz);
+        if (h->bcfg.balanced > 0) snprintf(bs, sizeof bs, "balanced split over %d blocks", h->bcfg.balanced);
+        else snprintf(bs, sizeof bs, "z chunks of %d planes", h->bcfg.tz);
+        snprintf(text, size_t(len), "gas: %s, %s; moments: %s, %s", gn, gs, bn, bs);
+    }
+    return FLIC_OK;
+}
+
+int flic_autotune(flic_handle* h, int reps, int use_cache, double* ms) {
+    if (!h || reps < 1) return FLIC_ERR_INVALID_ARG;
+    const TuneKey key = tune_key(h);
+    if (use_cache) {
+        std::pair<int, int> hit(-1, -1);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) hit = it->second;
+        }
+        if (hit.first >= 0) {
+            const int rc = flic_set_tile_config(h, hit.first, hit.second);
+            return rc ? rc : 1;
+        }
+    }
+    const int rc = h->fp64 ? tune_impl<double>(h, reps, ms) : tune_impl<float>(h, reps, ms);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(h->gcfg.cand, h->bcfg.cand);
+    return 0;
+}
+
 int flic_sync(flic_handle* h) {
     if (!h) return FLIC_ERR_INVALID_ARG;
     FLIC_CK(h, cudaStreamSynchronize(h->st));
@@ -496,7 +669,7 @@ const char* flic_last_error(flic_handle* h) {
 }
 
 const char* flic_version(void) {
-    return "libflic 0.1 (sm_103a; two-fluid FlIC/Godunov step, FFT Poisson)";
+    return "libflic 0.2 (sm_103a; two-fluid FlIC/Godunov step, FFT Poisson, launch-shape tuner)";
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 // step setup and the two-level reduction are one launch each for all runs.  A
 // step is captured once per state parity as a CUDA graph and replayed.
 #include <cmath>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -63,6 +64,9 @@ struct flic_ensemble {
     int nwork_gas = 0, nwork_bme = 0;
     RunScalars* prep_tab = nullptr;
     FinalizeArgs* fin_tab = nullptr;
+    // launch shapes of the fluid kernels (candidate index, z-chunk height cap)
+    int cand[2] = {0, 0};
+    int tz[2] = {32, 32};
     double* staging = nullptr;
     int cur = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -81,10 +85,9 @@ struct flic_ensemble {
 
 namespace {
 
+// Potentials of every run's current state (one set of FFT passes per size class).
 template <typename T>
-int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
-    if (ev) ENS_CK(e, cudaEventRecord(ev[0], e->st));
-    ENS_CK(e, step_prep_batch(e->prep_tab, e->nruns, dt, e->st));
+int ens_enqueue_poisson(flic_ensemble* e) {
     if (e->d.G != 0.0) {
         for (auto& c : e->classes) {
             const T* s = reinterpret_cast<const T*>(c.state[e->cur]);
@@ -100,12 +103,23 @@ int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
             }
         }
     }
+    return FLIC_OK;
+}
+
+template <typename T>
+int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
+    if (ev) ENS_CK(e, cudaEventRecord(ev[0], e->st));
+    ENS_CK(e, step_prep_batch(e->prep_tab, e->nruns, dt, e->st));
+    const int prc = ens_enqueue_poisson<T>(e);
+    if (prc) return prc;
     if (ev) ENS_CK(e, cudaEventRecord(ev[1], e->st));
-    ENS_CK(e, launch_gas_batch<T>(reinterpret_cast<const StencilArgs<T>*>(e->tab_gas[e->cur]), e->work_gas,
-                                  e->nwork_gas, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
+    ENS_CK(e, stencil_launch_batch<T>(FLUID_GAS, e->cand[FLUID_GAS],
+                                      reinterpret_cast<const StencilArgs<T>*>(e->tab_gas[e->cur]), e->work_gas,
+                                      e->nwork_gas, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[2], e->st));
-    ENS_CK(e, launch_bme_batch<T>(reinterpret_cast<const StencilArgs<T>*>(e->tab_bme[e->cur]), e->work_bme,
-                                  e->nwork_bme, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
+    ENS_CK(e, stencil_launch_batch<T>(FLUID_BME, e->cand[FLUID_BME],
+                                      reinterpret_cast<const StencilArgs<T>*>(e->tab_bme[e->cur]), e->work_bme,
+                                      e->nwork_bme, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[3], e->st));
     ENS_CK(e, step_finalize_batch(e->fin_tab, e->nruns, 1, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[4], e->st));
@@ -136,85 +150,31 @@ void ens_free(flic_ensemble* e) {
     if (e->own_stream && e->st) cudaStreamDestroy(e->st);
 }
 
+// (Re)builds what depends on the fluid kernels' launch shapes: each size
+// class's geometry, the work lists spanning all runs, the per-run partial rows
+// and the argument tables (the graphs are dropped).
 template <typename T>
-int ens_init(flic_ensemble* e) {
-    typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type C;
-    ENS_CK(e, stencil_prepare<T>());
-    // size classes in order of first appearance
-    for (int r = 0; r < e->nruns; ++r) {
-        int ci = -1;
-        for (size_t k = 0; k < e->classes.size(); ++k)
-            if (e->classes[k].N == e->run_n[r]) ci = int(k);
-        if (ci < 0) {
-            EnsClass c;
-            c.N = e->run_n[r];
-            e->classes.push_back(c);
-            ci = int(e->classes.size()) - 1;
-        }
-        e->run_class[r] = ci;
-        e->run_slot[r] = int(e->classes[ci].runs.size());
-        e->classes[ci].runs.push_back(r);
+int ens_build_work(flic_ensemble* e) {
+    for (int i = 0; i < 2; ++i) {
+        if (e->graph[i]) { cudaGraphExecDestroy(e->graph[i]); e->graph[i] = nullptr; }
+        if (e->tab_gas[i]) { cudaFree(e->tab_gas[i]); e->tab_gas[i] = nullptr; }
+        if (e->tab_bme[i]) { cudaFree(e->tab_bme[i]); e->tab_bme[i] = nullptr; }
     }
-    size_t max_cells = 0;
-    // per-run partial-row offsets
+    void* old[] = {e->work_gas, e->work_bme, e->part_gas, e->part_bme, e->prep_tab, e->fin_tab};
+    for (void* b : old)
+        if (b) cudaFree(b);
+    e->work_gas = e->work_bme = nullptr;
+    e->part_gas = e->part_bme = nullptr;
+    e->prep_tab = nullptr;
+    e->fin_tab = nullptr;
+    // (tile, z chunk) items: chunks of at most tz planes, so the work list of all
+    // runs fills the GPU
+    for (auto& c : e->classes) {
+        c.gcfg = stencil_cfg<T>(FLUID_GAS, e->cand[FLUID_GAS], c.N, c.N < e->tz[FLUID_GAS] ? c.N : e->tz[FLUID_GAS]);
+        c.bcfg = stencil_cfg<T>(FLUID_BME, e->cand[FLUID_BME], c.N, c.N < e->tz[FLUID_BME] ? c.N : e->tz[FLUID_BME]);
+    }
     std::vector<int> goff(e->nruns), boff(e->nruns);
     std::vector<WorkItem> wg, wb;
-    for (auto& c : e->classes) {
-        const int N = c.N;
-        if (fft_plan_init(N, &c.plans)) { e->err = "unsupported FFT length"; return FLIC_ERR_INVALID_ARG; }
-        if (e->iso && !fft_iso_supported(N)) { e->err = "unsupported size for the isolated solve"; return FLIC_ERR_INVALID_ARG; }
-        ENS_CK(e, fft_prepare<T>(N));
-        if (e->iso) ENS_CK(e, fft_prepare_iso<T>(N));
-        c.h = (e->d.box_max - e->d.box_min) / N;
-        const size_t cells = size_t(N) * N * N;
-        if (cells > max_cells) max_cells = cells;
-        c.fs = (cells + 63) / 64 * 64;
-        c.run_stride = F_COUNT * c.fs;
-        const int nb = int(c.runs.size());
-        const int L = e->iso ? 2 * N : N;
-        c.spec_stride = size_t(N) * L * (L / 2 + 1);
-        // z chunks of at most 32 planes: the work list of all runs fills the GPU
-        const int tz = N < 32 ? N : 32;
-        c.gcfg = gas_cfg<T>(N, tz);
-        c.bcfg = bme_cfg<T>(N, tz);
-        for (int i = 0; i < 2; ++i) {
-            ENS_CK(e, cudaMalloc(&c.state[i], c.run_stride * nb * sizeof(T)));
-            ENS_CK(e, cudaMemsetAsync(c.state[i], 0, c.run_stride * nb * sizeof(T), e->st));
-        }
-        ENS_CK(e, cudaMalloc(&c.phi, c.fs * nb * sizeof(T)));
-        ENS_CK(e, cudaMemsetAsync(c.phi, 0, c.fs * nb * sizeof(T), e->st));
-        ENS_CK(e, cudaMalloc(&c.spec, c.spec_stride * nb * sizeof(C)));
-        c.tw_len = L;
-        std::vector<C> tw(L);
-        for (int j = 0; j < L; ++j) {
-            const long double ang = 2.0L * 3.141592653589793238462643383279502884L * j / L;
-            tw[j].x = T(std::cos(ang));
-            tw[j].y = T(-std::sin(ang));
-        }
-        ENS_CK(e, cudaMalloc(&c.tw, L * sizeof(C)));
-        ENS_CK(e, cudaMemcpy(c.tw, tw.data(), L * sizeof(C), cudaMemcpyHostToDevice));
-        std::vector<T> a2(N);
-        for (int k = 0; k < N; ++k) {
-            const long double s = std::sin(3.141592653589793238462643383279502884L * k / N);
-            a2[k] = T((2.0L / 3.0L) * s * s);
-        }
-        ENS_CK(e, cudaMalloc(&c.asin2, N * sizeof(T)));
-        ENS_CK(e, cudaMemcpy(c.asin2, a2.data(), N * sizeof(T), cudaMemcpyHostToDevice));
-        if (e->iso) {
-            ENS_CK(e, cudaMalloc(&c.gtab, green_table_elems<T>(N) * sizeof(T)));
-            void* greal = nullptr;
-            void* gspec = nullptr;
-            cudaError_t er = cudaMalloc(&greal, size_t(L) * L * L * sizeof(T));
-            if (er == cudaSuccess) er = cudaMalloc(&gspec, size_t(L) * L * (L / 2 + 1) * sizeof(C));
-            if (er == cudaSuccess)
-                er = green_init<T>(N, c.h, e->d.G, reinterpret_cast<T*>(c.gtab), reinterpret_cast<T*>(greal), gspec,
-                                   c.tw, e->st);
-            if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
-            if (greal) cudaFree(greal);
-            if (gspec) cudaFree(gspec);
-            ENS_CK(e, er);
-        }
-    }
     // work lists and partial rows
     int pg = 0, pb = 0;
     for (int r = 0; r < e->nruns; ++r) {
@@ -239,17 +199,6 @@ int ens_init(flic_ensemble* e) {
     ENS_CK(e, cudaMalloc(&e->part_bme, size_t(pb) * Q_COUNT * sizeof(double)));
     ENS_CK(e, cudaMemsetAsync(e->part_gas, 0, size_t(pg) * Q_COUNT * sizeof(double), e->st));
     ENS_CK(e, cudaMemsetAsync(e->part_bme, 0, size_t(pb) * Q_COUNT * sizeof(double), e->st));
-    e->nb_diag = 152 * 4;
-    ENS_CK(e, cudaMalloc(&e->part_diag, size_t(e->nb_diag) * Q_COUNT * sizeof(double)));
-    ENS_CK(e, cudaMalloc(&e->scal, size_t(e->nruns) * S_COUNT * sizeof(double)));
-    ENS_CK(e, cudaMemsetAsync(e->scal, 0, size_t(e->nruns) * S_COUNT * sizeof(double), e->st));
-    ENS_CK(e, cudaMalloc(&e->status, size_t(e->nruns) * sizeof(unsigned int)));
-    ENS_CK(e, cudaMemsetAsync(e->status, 0, size_t(e->nruns) * sizeof(unsigned int), e->st));
-    ENS_CK(e, cudaMalloc(&e->diag, size_t(e->nruns) * sizeof(flic_diag)));
-    ENS_CK(e, cudaMemsetAsync(e->diag, 0, size_t(e->nruns) * sizeof(flic_diag), e->st));
-    ENS_CK(e, cudaMallocHost(&e->diag_host, size_t(e->nruns) * sizeof(flic_diag)));
-    ENS_CK(e, cudaMalloc(&e->level1, size_t(e->nruns) * FINALIZE_ROWS * Q_COUNT * sizeof(double)));
-    ENS_CK(e, cudaMalloc(&e->staging, max_cells * sizeof(double)));
     // per-run argument tables
     std::vector<RunScalars> prep(e->nruns);
     std::vector<FinalizeArgs> fin(e->nruns);
@@ -309,6 +258,179 @@ int ens_init(flic_ensemble* e) {
     ENS_CK(e, cudaMemcpy(e->fin_tab, fin.data(), e->nruns * sizeof(FinalizeArgs), cudaMemcpyHostToDevice));
     ENS_CK(e, cudaStreamSynchronize(e->st));
     return FLIC_OK;
+}
+
+template <typename T>
+int ens_init(flic_ensemble* e) {
+    typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type C;
+    ENS_CK(e, stencil_prepare<T>());
+    // size classes in order of first appearance
+    for (int r = 0; r < e->nruns; ++r) {
+        int ci = -1;
+        for (size_t k = 0; k < e->classes.size(); ++k)
+            if (e->classes[k].N == e->run_n[r]) ci = int(k);
+        if (ci < 0) {
+            EnsClass c;
+            c.N = e->run_n[r];
+            e->classes.push_back(c);
+            ci = int(e->classes.size()) - 1;
+        }
+        e->run_class[r] = ci;
+        e->run_slot[r] = int(e->classes[ci].runs.size());
+        e->classes[ci].runs.push_back(r);
+    }
+    size_t max_cells = 0;
+    // per-run partial-row offsets
+    std::vector<int> goff(e->nruns), boff(e->nruns);
+    std::vector<WorkItem> wg, wb;
+    for (auto& c : e->classes) {
+        const int N = c.N;
+        if (fft_plan_init(N, &c.plans)) { e->err = "unsupported FFT length"; return FLIC_ERR_INVALID_ARG; }
+        if (e->iso && !fft_iso_supported(N)) { e->err = "unsupported size for the isolated solve"; return FLIC_ERR_INVALID_ARG; }
+        ENS_CK(e, fft_prepare<T>(N));
+        if (e->iso) ENS_CK(e, fft_prepare_iso<T>(N));
+        c.h = (e->d.box_max - e->d.box_min) / N;
+        const size_t cells = size_t(N) * N * N;
+        if (cells > max_cells) max_cells = cells;
+        c.fs = (cells + 63) / 64 * 64;
+        c.run_stride = F_COUNT * c.fs;
+        const int nb = int(c.runs.size());
+        const int L = e->iso ? 2 * N : N;
+        c.spec_stride = size_t(N) * L * (L / 2 + 1);
+        for (int i = 0; i < 2; ++i) {
+            ENS_CK(e, cudaMalloc(&c.state[i], c.run_stride * nb * sizeof(T)));
+            ENS_CK(e, cudaMemsetAsync(c.state[i], 0, c.run_stride * nb * sizeof(T), e->st));
+        }
+        ENS_CK(e, cudaMalloc(&c.phi, c.fs * nb * sizeof(T)));
+        ENS_CK(e, cudaMemsetAsync(c.phi, 0, c.fs * nb * sizeof(T), e->st));
+        ENS_CK(e, cudaMalloc(&c.spec, c.spec_stride * nb * sizeof(C)));
+        c.tw_len = L;
+        std::vector<C> tw(L);
+        for (int j = 0; j < L; ++j) {
+            const long double ang = 2.0L * 3.141592653589793238462643383279502884L * j / L;
+            tw[j].x = T(std::cos(ang));
+            tw[j].y = T(-std::sin(ang));
+        }
+        ENS_CK(e, cudaMalloc(&c.tw, L * sizeof(C)));
+        ENS_CK(e, cudaMemcpy(c.tw, tw.data(), L * sizeof(C), cudaMemcpyHostToDevice));
+        std::vector<T> a2(N);
+        for (int k = 0; k < N; ++k) {
+            const long double s = std::sin(3.141592653589793238462643383279502884L * k / N);
+            a2[k] = T((2.0L / 3.0L) * s * s);
+        }
+        ENS_CK(e, cudaMalloc(&c.asin2, N * sizeof(T)));
+        ENS_CK(e, cudaMemcpy(c.asin2, a2.data(), N * sizeof(T), cudaMemcpyHostToDevice));
+        if (e->iso) {
+            ENS_CK(e, cudaMalloc(&c.gtab, green_table_elems<T>(N) * sizeof(T)));
+            void* greal = nullptr;
+            void* gspec = nullptr;
+            cudaError_t er = cudaMalloc(&greal, size_t(L) * L * L * sizeof(T));
+            if (er == cudaSuccess) er = cudaMalloc(&gspec, size_t(L) * L * (L / 2 + 1) * sizeof(C));
+            if (er == cudaSuccess)
+                er = green_init<T>(N, c.h, e->d.G, reinterpret_cast<T*>(c.gtab), reinterpret_cast<T*>(greal), gspec,
+                                   c.tw, e->st);
+            if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
+            if (greal) cudaFree(greal);
+            if (gspec) cudaFree(gspec);
+            ENS_CK(e, er);
+        }
+    }
+    ENS_CK(e, cudaMalloc(&e->staging, max_cells * sizeof(double)));
+    e->nb_diag = 152 * 4;
+    ENS_CK(e, cudaMalloc(&e->part_diag, size_t(e->nb_diag) * Q_COUNT * sizeof(double)));
+    ENS_CK(e, cudaMalloc(&e->scal, size_t(e->nruns) * S_COUNT * sizeof(double)));
+    ENS_CK(e, cudaMemsetAsync(e->scal, 0, size_t(e->nruns) * S_COUNT * sizeof(double), e->st));
+    ENS_CK(e, cudaMalloc(&e->status, size_t(e->nruns) * sizeof(unsigned int)));
+    ENS_CK(e, cudaMemsetAsync(e->status, 0, size_t(e->nruns) * sizeof(unsigned int), e->st));
+    ENS_CK(e, cudaMalloc(&e->diag, size_t(e->nruns) * sizeof(flic_diag)));
+    ENS_CK(e, cudaMemsetAsync(e->diag, 0, size_t(e->nruns) * sizeof(flic_diag), e->st));
+    ENS_CK(e, cudaMallocHost(&e->diag_host, size_t(e->nruns) * sizeof(flic_diag)));
+    ENS_CK(e, cudaMalloc(&e->level1, size_t(e->nruns) * FINALIZE_ROWS * Q_COUNT * sizeof(double)));
+    const int rc = ens_build_work<T>(e);
+    if (rc) return rc;
+    ENS_CK(e, cudaStreamSynchronize(e->st));
+    return FLIC_OK;
+}
+
+// z-chunk height caps the ensemble tuner tries with every candidate shape
+constexpr int ENS_TZ_OPTIONS[3] = {16, 32, 64};
+
+// Times every (candidate shape, chunk cap) of both fluid kernels over the whole
+// work list on the current states and keeps the fastest of each kernel.  The
+// launches write the spare state buffers only.
+template <typename T>
+int ens_tune(flic_ensemble* e, int reps, double* ms) {
+    ENS_CK(e, step_prep_batch(e->prep_tab, e->nruns, 0.0, e->st));
+    int rc = ens_enqueue_poisson<T>(e);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ENS_CK(e, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        ENS_CK(e, ce);
+    }
+    int k = 0;
+    int best_c[2] = {e->cand[0], e->cand[1]}, best_t[2] = {e->tz[0], e->tz[1]};
+    for (int fluid = 0; fluid < 2 && rc == FLIC_OK; ++fluid) {
+        int nc = 0;
+        stencil_cands<T>(fluid, &nc);
+        double best_ms = -1.0;
+        const StencilCand<T>* cands = stencil_cands<T>(fluid, &nc);
+        for (int c = 0; c < nc && rc == FLIC_OK; ++c) {
+            // entries that differ only in the single-grid split are one compiled shape here
+            bool seen = false;
+            for (int c2 = 0; c2 < c; ++c2) seen = seen || cands[c2].launch_batch == cands[c].launch_batch;
+            if (seen) {
+                for (int t = 0; t < 3; ++t, ++k)
+                    if (ms) ms[k] = -1.0;
+                continue;
+            }
+            for (int t = 0; t < 3; ++t, ++k) {
+                e->cand[fluid] = c;
+                e->tz[fluid] = ENS_TZ_OPTIONS[t];
+                rc = ens_build_work<T>(e);
+                if (rc) break;
+                const bool gas = fluid == FLUID_GAS;
+                const StencilArgs<T>* tab = reinterpret_cast<const StencilArgs<T>*>(gas ? e->tab_gas[e->cur]
+                                                                                          : e->tab_bme[e->cur]);
+                const WorkItem* work = gas ? e->work_gas : e->work_bme;
+                const int nwork = gas ? e->nwork_gas : e->nwork_bme;
+                const bool out = e->d.hydro_bc == FLIC_HYDRO_OUTFLOW;
+                cudaError_t er = stencil_launch_batch<T>(fluid, c, tab, work, nwork, out, e->st);
+                if (er == cudaSuccess) er = cudaEventRecord(e0, e->st);
+                for (int r = 0; r < reps && er == cudaSuccess; ++r)
+                    er = stencil_launch_batch<T>(fluid, c, tab, work, nwork, out, e->st);
+                if (er == cudaSuccess) er = cudaEventRecord(e1, e->st);
+                if (er == cudaSuccess) er = cudaEventSynchronize(e1);
+                float el = 0.f;
+                if (er == cudaSuccess) er = cudaEventElapsedTime(&el, e0, e1);
+                double tm = -1.0;
+                if (er == cudaSuccess) {
+                    tm = double(el) / reps;
+                } else if (er == cudaErrorInvalidConfiguration || er == cudaErrorLaunchOutOfResources ||
+                           er == cudaErrorInvalidValue) {
+                    cudaGetLastError();   // a shape this device cannot launch: skipped
+                } else {
+                    e->err = std::string("launch-shape tuning: ") + cudaGetErrorString(er);
+                    rc = FLIC_ERR_CUDA;
+                    break;
+                }
+                if (ms) ms[k] = tm;
+                if (tm >= 0.0 && (best_ms < 0.0 || tm < best_ms)) {
+                    best_ms = tm;
+                    best_c[fluid] = c;
+                    best_t[fluid] = ENS_TZ_OPTIONS[t];
+                }
+            }
+        }
+        e->cand[fluid] = best_c[fluid];
+        e->tz[fluid] = best_t[fluid];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    return ens_build_work<T>(e);
 }
 
 template <typename T>
@@ -507,6 +629,64 @@ int flic_ensemble_launches_per_step(flic_ensemble* e) {
     if (!e) return FLIC_ERR_INVALID_ARG;
     // setup, five FFT passes per size class, two fluid launches, two-level reduction
     return 1 + (e->d.G != 0.0 ? 5 * int(e->classes.size()) : 0) + 2 + 2;
+}
+
+int flic_ensemble_autotune(flic_ensemble* e, int reps, double* ms) {
+    if (!e || reps < 1) return FLIC_ERR_INVALID_ARG;
+    return e->fp64 ? ens_tune<double>(e, reps, ms) : ens_tune<float>(e, reps, ms);
+}
+
+int flic_ensemble_num_tile_configs(flic_ensemble* e, int* n_gas, int* n_bme) {
+    if (!e || !n_gas || !n_bme) return FLIC_ERR_INVALID_ARG;
+    if (e->fp64) {
+        stencil_cands<double>(FLUID_GAS, n_gas);
+        stencil_cands<double>(FLUID_BME, n_bme);
+    } else {
+        stencil_cands<float>(FLUID_GAS, n_gas);
+        stencil_cands<float>(FLUID_BME, n_bme);
+    }
+    return FLIC_OK;
+}
+
+int flic_ensemble_set_tile_config(flic_ensemble* e, int gas, int bme, int tz_gas, int tz_bme) {
+    if (!e) return FLIC_ERR_INVALID_ARG;
+    int ng = 0, nb = 0;
+    if (e->fp64) {
+        stencil_cands<double>(FLUID_GAS, &ng);
+        stencil_cands<double>(FLUID_BME, &nb);
+    } else {
+        stencil_cands<float>(FLUID_GAS, &ng);
+        stencil_cands<float>(FLUID_BME, &nb);
+    }
+    if (gas < -1 || gas >= ng || bme < -1 || bme >= nb || tz_gas == 0 || tz_bme == 0 || tz_gas < -1 ||
+        tz_bme < -1) {
+        e->err = "launch shape index or chunk height out of range";
+        return FLIC_ERR_INVALID_ARG;
+    }
+    if (gas >= 0) e->cand[FLUID_GAS] = gas;
+    if (bme >= 0) e->cand[FLUID_BME] = bme;
+    if (tz_gas > 0) e->tz[FLUID_GAS] = tz_gas;
+    if (tz_bme > 0) e->tz[FLUID_BME] = tz_bme;
+    ENS_CK(e, cudaStreamSynchronize(e->st));
+    return e->fp64 ? ens_build_work<double>(e) : ens_build_work<float>(e);
+}
+
+int flic_ensemble_tile_config(flic_ensemble* e, int* gas, int* bme, int* tz_gas, int* tz_bme, char* text, int len) {
+    if (!e) return FLIC_ERR_INVALID_ARG;
+    if (gas) *gas = e->cand[FLUID_GAS];
+    if (bme) *bme = e->cand[FLUID_BME];
+    if (tz_gas) *tz_gas = e->tz[FLUID_GAS];
+    if (tz_bme) *tz_bme = e->tz[FLUID_BME];
+    if (text && len > 0) {
+        int n = 0;
+        const char* gn = e->fp64 ? stencil_cands<double>(FLUID_GAS, &n)[e->cand[FLUID_GAS]].name
+                                 : stencil_cands<float>(FLUID_GAS, &n)[e->cand[FLUID_GAS]].name;
+        const char* bn = e->fp64 ? stencil_cands<double>(FLUID_BME, &n)[e->cand[FLUID_BME]].name
+                                 : stencil_cands<float>(FLUID_BME, &n)[e->cand[FLUID_BME]].name;
+        snprintf(text, size_t(len), "gas: %s, work items of at most %d planes; moments: %s, work items of at most %d planes",
+                 gn, e->tz[FLUID_GAS], bn, e->tz[FLUID_BME]);
+    }
+    return FLIC_OK;
 }
 
 int flic_ensemble_destroy(flic_ensemble* e) {

@@ -9,29 +9,53 @@
 
 namespace flic {
 
-// Launch geometry of one fluid kernel: tiles of TX x TY columns, z chunks of tz planes.
+// Launch geometry of one fluid kernel: the compiled launch shape (index into
+// the fluid's candidate table), tiles of TX x TY columns, z chunks of tz planes.
 struct StepCfg {
-    int tx, ty;        // tile shape
-    int tiles_x, tiles_y;
-    int tz, blocks_z;     // tz = 0: balanced split over `balanced` blocks
+    int cand = 0;
+    int tx = 0, ty = 0;   // tile shape
+    int tiles_x = 0, tiles_y = 0;
+    int tz = 0, blocks_z = 0;   // tz = 0: balanced split over `balanced` blocks
     int balanced = 0;
-    int threads;
-    size_t smem;
+    int threads = 0;
+    size_t smem = 0;
     int num_blocks() const { return balanced > 0 ? balanced : tiles_x * tiles_y * blocks_z; }
 };
 
-template <typename T> cudaError_t stencil_prepare();   // shared-memory limits, once
-template <typename T> StepCfg gas_cfg(int N, int tz);
-template <typename T> StepCfg bme_cfg(int N, int tz);
-template <typename T> cudaError_t launch_gas(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
-template <typename T> cudaError_t launch_bme(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
+enum Fluid { FLUID_GAS = 0, FLUID_BME = 1 };
+// How a single grid's z planes are split over blocks (a batched ensemble always
+// uses (tile, chunk) work items).
+enum Split { SPLIT_CHUNK = 0, SPLIT_BALANCED = 1 };
+
+// One compiled launch shape of a fluid kernel (tile, threads, occupancy, staging)
+// together with the z split it is used with on a single grid: an entry of the
+// candidate table that the launch-shape tuner times.  Entry 0 of each table is
+// the default.
+template <typename T>
+struct StencilCand {
+    const char* name;
+    int split;
+    StepCfg (*cfg)(int N, int tz, int split);
+    cudaError_t (*prepare)();
+    cudaError_t (*launch)(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
+    cudaError_t (*launch_batch)(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
+                                cudaStream_t st);
+};
+template <typename T> const StencilCand<T>* gas_cands(int* count);
+template <typename T> const StencilCand<T>* bme_cands(int* count);
+template <typename T> const StencilCand<T>* stencil_cands(int fluid, int* count) {
+    return fluid == FLUID_GAS ? gas_cands<T>(count) : bme_cands<T>(count);
+}
+
+template <typename T> cudaError_t stencil_prepare();   // shared-memory limits of every candidate, once
+// Geometry of candidate `cand` on an N^3 grid; tz > 0 forces (tile, chunk) work
+// of that height (batched ensembles), tz <= 0 uses the candidate's split.
+template <typename T> StepCfg stencil_cfg(int fluid, int cand, int N, int tz);
+template <typename T> cudaError_t stencil_launch(int fluid, const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
 // One launch over a work list spanning several runs (table and work in device memory).
 template <typename T>
-cudaError_t launch_gas_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
-                             cudaStream_t st);
-template <typename T>
-cudaError_t launch_bme_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
-                             cudaStream_t st);
+cudaError_t stencil_launch_batch(int fluid, int cand, const StencilArgs<T>* table, const WorkItem* work, int nwork,
+                                 bool outflow, cudaStream_t st);
 
 // float64 <-> storage precision conversion of one field.
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);

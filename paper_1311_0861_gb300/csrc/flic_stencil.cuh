@@ -376,15 +376,16 @@ constexpr int RING_SLOTS = 3;   // planes e, e+1 in use, e+2 in flight
 // Launch shape of a fluid kernel: TX x TY column tile, minimum resident blocks
 // per SM (register budget), whether the moment energy tensor is staged in
 // shared memory (SEX), whether the block has one thread per updated cell (WIDE;
-// else one per tile cell, looping over the border cells), how many x/y faces
-// each thread without a tile cell takes first (HR) and whether a single grid is
-// split evenly over one block per resident slot (BAL) or as a (tile, z chunk)
-// grid (which keeps neighbouring tiles at the same planes, sharing their halos
-// in L2).
-template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_, bool BAL_ = false>
+// else one per tile cell, looping over the border cells) and how many x/y faces
+// each thread without a tile cell takes first (HR).  How the z planes of a grid
+// are split over blocks is chosen at launch (StepCfg).
+// With DB the transported state f' and the x/y face buffers are double-buffered
+// by plane parity, which lets one barrier per plane separate the stages (see
+// the kernel).
+template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_, bool DB_ = false>
 struct TileCfg {
     static constexpr int TX = TX_, TY = TY_, MINB = MINB_, HR = HR_;
-    static constexpr bool SEX = SEX_, WIDE = WIDE_, BAL = BAL_;
+    static constexpr bool SEX = SEX_, WIDE = WIDE_, DB = DB_;
 };
 
 template <class P, typename T, class C>
@@ -407,11 +408,16 @@ struct Geom {
     static constexpr int CH = 8 / sizeof(T);                         // elements per 8-byte copy
     static constexpr int CPR = W2 / CH;                              // copies per ring row
     static_assert(W2 % CH == 0, "ring rows must split into 8-byte copies");
+    static constexpr int NBUF = C::DB ? 2 : 1;                      // copies of f' and the x/y faces
+    static_assert(!(C::DB && SEX), "the staged energy tensor has no slot for the one-barrier schedule");
     static constexpr size_t ring_elems = size_t(RING_SLOTS) * P::NR * R2;
-    static constexpr size_t xf_elems = size_t(P::NFACE) * H1 * XFW;
-    static constexpr size_t yf_elems = size_t(P::NFACE) * YFH * W1;
+    static constexpr size_t xf_one = size_t(P::NFACE) * H1 * XFW;
+    static constexpr size_t yf_one = size_t(P::NFACE) * YFH * W1;
+    static constexpr size_t fp_one = size_t(P::NF) * R1;
+    static constexpr size_t xf_elems = NBUF * xf_one;
+    static constexpr size_t yf_elems = NBUF * yf_one;
     static constexpr size_t zc_elems = size_t(P::NFACE) * R1;
-    static constexpr size_t fp_elems = size_t(P::NF) * R1;
+    static constexpr size_t fp_elems = NBUF * fp_one;
     static constexpr size_t phim_elems = R1;
     // fields read only by the Eulerian update (moment energy tensor), staged
     // over the R1 rows in two slots when SEX
@@ -492,8 +498,9 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     // pressure past the 128-register budget), so it keeps scalar rows.
     constexpr bool PK = std::is_same<T, float>::value && P::NF % 2 == 0;
     constexpr bool FP2 = PK && P::NF < 16;
-    static_assert(!FP2 || (Gm::ring_elems + Gm::xf_elems + Gm::yf_elems + Gm::zc_elems) % 2 == 0,
-                  "the f' buffer must start on an 8-byte boundary");
+    static_assert(!FP2 || ((Gm::ring_elems + Gm::xf_elems + Gm::yf_elems + Gm::zc_elems) % 2 == 0 &&
+                           Gm::fp_one % 2 == 0),
+                  "the f' buffers must start on an 8-byte boundary");
     constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE, NEX = P::NEX;
     constexpr int NXF = Gm::H1 * Gm::XFW;
     constexpr int NYF = Gm::YFH * W1;
@@ -694,196 +701,234 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         // round-robin over all threads.
         constexpr int NH = NTH - NT;
         constexpr int HF = (NH * C::HR < NXF + NYF) ? NH * C::HR : NXF + NYF;
-        auto face_item = [&](const T* rpe, int i) {
+        auto face_item = [&](const T* rpe, T* xfo, T* yfo, int i) {
             T v[NFACE];
             if (i < NXF) {
                 const int fx = i % Gm::XFW, jy = i / Gm::XFW;
                 const int a2 = (jy + 1) * W2 + fx;
                 P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) xf[k * NXF + i] = v[k];
+                for (int k = 0; k < NFACE; ++k) xfo[k * NXF + i] = v[k];
             } else {
                 const int j = i - NXF;
                 const int jx = j % W1, fy = j / W1;
                 const int a2 = fy * W2 + jx + 1;
                 P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) yf[k * NYF + j] = v[k];
+                for (int k = 0; k < NFACE; ++k) yfo[k * NYF + j] = v[k];
             }
         };
-        auto xy_faces = [&](const T* rpe) {
+        // face buffers and f' buffer of plane p (by parity with DB)
+        auto xf_of = [&](int p) { return xf + (C::DB ? (p & 1) * Gm::xf_one : 0); };
+        auto yf_of = [&](int p) { return yf + (C::DB ? (p & 1) * Gm::yf_one : 0); };
+        auto fp_of = [&](int p) { return fpb + (C::DB ? (p & 1) * Gm::fp_one : 0); };
+        auto xy_faces = [&](const T* rpe, int pe) {
+            T* xfo = xf_of(pe);
+            T* yfo = yf_of(pe);
             if constexpr (NH > 0) {
                 if (!own_tile)
-                    for (int i = tid - NT; i < HF; i += NH) face_item(rpe, i);
+                    for (int i = tid - NT; i < HF; i += NH) face_item(rpe, xfo, yfo, i);
             }
-            for (int i = HF + tid; i < NXF + NYF; i += NTH) face_item(rpe, i);
+            for (int i = HF + tid; i < NXF + NYF; i += NTH) face_item(rpe, xfo, yfo, i);
         };
 
-        // Two barriers per plane.  Iteration e:
-        //   [copies of planes e, e+1 landed; barrier]
-        //   phase 1: z faces e+1/2 and the Eulerian update of plane e over R1 (S2)
-        //   [barrier]
-        //   phase 2: Lagrangian fluxes of the own cell at plane e (S3), then the x/y
-        //            faces of plane e+1 (S1) -- the own cell's face velocities were
-        //            kept in registers in phase 1, so the face buffers can be reused
-        issue_plane(z0 - 2);
-        issue_plane(z0 - 1);
         T Wxm = T(0), Wxp = T(0), Wym = T(0), Wyp = T(0);
-        for (int e = z0 - 2; e <= z1; ++e) {
+
+        // Phase 1 of plane e: the z face e+1/2 and the Eulerian update of plane e
+        // over R1 (S2), f' into the plane's buffer; the own tile cell keeps its
+        // face normal velocities for its Lagrangian fluxes.
+        auto phase1 = [&](int e) {
             const T* re = ring + ring_slot(e) * NR * R2;       // plane e
             const T* rp = ring + ring_slot(e + 1) * NR * R2;   // plane e + 1
-            // plane e + 2 goes into the slot of plane e - 1 (last read in phase 1
-            // of the previous iteration); the staged extra fields of plane e + 1
-            // (read in phase 1 of the next iteration) travel in the same group
-            if (e + 2 <= z1 + 1) {
-                if (SEX && NEX > 0 && e + 1 >= z0 - 1) issue_extra(e + 1);
-                issue_plane(e + 2);
-                cp_async_wait<1>();
+            const bool active = (e >= z0 - 1);                // f' of plane e is needed
+            const T* xfe = xf_of(e);
+            const T* yfe = yf_of(e);
+            T* fpo = fp_of(e);
+            const size_t zoff_e = size_t(plane_of(e)) * plane;
+            for (int i = tid; i < NU; i += NTH) {
+                int jx, jy;
+                r1_coords<TX, TY>(i, jx, jy);
+                const int c1 = jy * W1 + jx;
+                const int c2 = (jy + 1) * W2 + jx + 1;
+                T ex[NEX > 0 ? NEX : 1];
+                if (active) {
+                    if constexpr (PREF) {
+#pragma unroll
+                        for (int k = 0; k < NEX; ++k) ex[k] = exn[k];
+                        if (e + 1 <= z1) load_ex(e + 1);
+                    } else if (SEX) {
+                        const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
+#pragma unroll
+                        for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
+                    } else {
+                        const size_t g = zoff_e + size_t(yoff[jy + 1]) + gx(jx + 1);
+#pragma unroll
+                        for (int k = 0; k < NEX; ++k) ex[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
+                    }
+                }
+                T zn[NFACE];
+                P::face(re, c2, rp, c2, R2, 2, gamma, zn);
+                if (active) {
+                    T fm[3][NFACE], fpv[3][NFACE];
+#pragma unroll
+                    for (int k = 0; k < NFACE; ++k) {
+                        fm[0][k] = xfe[k * NXF + jy * Gm::XFW + jx];
+                        fpv[0][k] = xfe[k * NXF + jy * Gm::XFW + jx + 1];
+                        fm[1][k] = yfe[k * NYF + jy * W1 + jx];
+                        fpv[1][k] = yfe[k * NYF + (jy + 1) * W1 + jx];
+                        fm[2][k] = zc[k * R1 + c1];
+                        fpv[2][k] = zn[k];
+                    }
+                    T g[3];
+                    g[0] = (re[P::R_PHI * R2 + c2 + 1] - re[P::R_PHI * R2 + c2 - 1]) * half_ih;
+                    g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
+                    g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
+                    T f1[NF];
+                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
+                    if constexpr (FP2) {
+                        // field pairs side by side: one 8-byte store per pair
+#pragma unroll
+                        for (int f = 0; f < NF; f += 2)
+                            reinterpret_cast<float2*>(fpo)[(f / 2) * R1 + c1] = make_float2(f1[f], f1[f + 1]);
+                    } else {
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) fpo[f * R1 + c1] = f1[f];
+                    }
+                    if (i < NT) {
+                        // own tile cell (i == tid): keep its face normal velocities for S3
+                        // (gas: V first on every axis; moments: u*_d is value d)
+                        wz_prev = P::normal_velocity(fm[2], 2);
+                        Wxm = P::normal_velocity(fm[0], 0);
+                        Wxp = P::normal_velocity(fpv[0], 0);
+                        Wym = P::normal_velocity(fm[1], 1);
+                        Wyp = P::normal_velocity(fpv[1], 1);
+                        if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
+                phim[c1] = re[P::R_PHI * R2 + c2];
+            }
+        };
+
+        // S3 of plane e for the own tile cell: Lagrangian fluxes of f'_e (its own
+        // column and four lateral neighbours) with the face velocities kept by
+        // phase 1 of plane e; completes plane e - 1 (energy balance, store).
+        auto s3 = [&](int e) {
+            const T* fpi = fp_of(e);
+            const T Wzm = wz_prev;
+            // upwind cell of each lateral face (the own cell where the face
+            // velocity points away from it)
+            const int cxm = own_c1 - (Wxm > T(0) ? 1 : 0);
+            const int cxp = own_c1 + (Wxp > T(0) ? 0 : 1);
+            const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
+            const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
+            T out[NF];
+            if constexpr (PK) {
+                // fields in pairs with packed float32 arithmetic (one instruction
+                // for two fields); the same operations as the scalar form below
+                const float2 wz = make_float2(Wzm, Wzm), nr = make_float2(-rat, -rat), pr = make_float2(rat, rat);
+                const float2 wxp = make_float2(Wxp, Wxp), nwxm = make_float2(-Wxm, -Wxm);
+                const float2 wyp = make_float2(Wyp, Wyp), nwym = make_float2(-Wym, -Wym);
+                const bool zup = Wzm > T(0);
+#pragma unroll
+                for (int f = 0; f < NF; f += 2) {
+                    float2 fc, uxm, uxp, uym, uyp;
+                    if constexpr (FP2) {
+                        const float2* F2 = reinterpret_cast<const float2*>(fpi) + (f / 2) * R1;
+                        fc = F2[own_c1];
+                        uxm = F2[cxm];
+                        uxp = F2[cxp];
+                        uym = F2[cym];
+                        uyp = F2[cyp];
+                    } else {
+                        const T* F0 = fpi + f * R1;
+                        const T* F1 = F0 + R1;
+                        fc = make_float2(F0[own_c1], F1[own_c1]);
+                        uxm = make_float2(F0[cxm], F1[cxm]);
+                        uxp = make_float2(F0[cxp], F1[cxp]);
+                        uym = make_float2(F0[cym], F1[cym]);
+                        uyp = make_float2(F0[cyp], F1[cyp]);
+                    }
+                    const float2 Fzm = __fmul2_rn(wz, zup ? make_float2(fprev[f], fprev[f + 1]) : fc);
+                    const float2 o = __ffma2_rn(nr, Fzm, make_float2(acc[f], acc[f + 1]));   // completes plane e-1
+                    float2 t = __fadd2_rn(__ffma2_rn(nwxm, uxm, __fmul2_rn(wxp, uxp)),
+                                          __ffma2_rn(nwym, uym, __fmul2_rn(wyp, uyp)));
+                    const float2 n2 = __ffma2_rn(pr, Fzm, __ffma2_rn(nr, t, fc));
+                    out[f] = o.x;
+                    out[f + 1] = o.y;
+                    acc[f] = n2.x;
+                    acc[f + 1] = n2.y;
+                    fprev[f] = fc.x;
+                    fprev[f + 1] = fc.y;
+                }
             } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            const bool active = (e >= z0 - 1);   // f' of plane e is needed
-            // ---- phase 1: z face e+1/2 and Eulerian update of plane e over R1 ----
-            {
-                const size_t zoff_e = size_t(plane_of(e)) * plane;
-                for (int i = tid; i < NU; i += NTH) {
-                    int jx, jy;
-                    r1_coords<TX, TY>(i, jx, jy);
-                    const int c1 = jy * W1 + jx;
-                    const int c2 = (jy + 1) * W2 + jx + 1;
-                    T ex[NEX > 0 ? NEX : 1];
-                    if (active) {
-                        if constexpr (PREF) {
 #pragma unroll
-                            for (int k = 0; k < NEX; ++k) ex[k] = exn[k];
-                            if (e + 1 <= z1) load_ex(e + 1);
-                        } else if (SEX) {
-                            const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
-#pragma unroll
-                            for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
-                        } else {
-                            const size_t g = zoff_e + size_t(yoff[jy + 1]) + gx(jx + 1);
-#pragma unroll
-                            for (int k = 0; k < NEX; ++k) ex[k] = __ldg(a.in + size_t(P::extra_field(k)) * a.fs + g);
-                        }
-                    }
-                    T zn[NFACE];
-                    P::face(re, c2, rp, c2, R2, 2, gamma, zn);
-                    if (active) {
-                        T fm[3][NFACE], fpv[3][NFACE];
-#pragma unroll
-                        for (int k = 0; k < NFACE; ++k) {
-                            fm[0][k] = xf[k * NXF + jy * Gm::XFW + jx];
-                            fpv[0][k] = xf[k * NXF + jy * Gm::XFW + jx + 1];
-                            fm[1][k] = yf[k * NYF + jy * W1 + jx];
-                            fpv[1][k] = yf[k * NYF + (jy + 1) * W1 + jx];
-                            fm[2][k] = zc[k * R1 + c1];
-                            fpv[2][k] = zn[k];
-                        }
-                        T g[3];
-                        g[0] = (re[P::R_PHI * R2 + c2 + 1] - re[P::R_PHI * R2 + c2 - 1]) * half_ih;
-                        g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
-                        g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
-                        T f1[NF];
-                        P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
-#pragma unroll
-                        if constexpr (FP2) {
-                            // field pairs side by side: one 8-byte store per pair
-#pragma unroll
-                            for (int f = 0; f < NF; f += 2)
-                                reinterpret_cast<float2*>(fpb)[(f / 2) * R1 + c1] = make_float2(f1[f], f1[f + 1]);
-                        } else {
-#pragma unroll
-                            for (int f = 0; f < NF; ++f) fpb[f * R1 + c1] = f1[f];
-                        }
-                        if (i < NT) {
-                            // own tile cell (i == tid): keep its face normal velocities for phase 2
-                            // (gas: V first on every axis; moments: u*_d is value d)
-                            wz_prev = P::normal_velocity(fm[2], 2);
-                            Wxm = P::normal_velocity(fm[0], 0);
-                            Wxp = P::normal_velocity(fpv[0], 0);
-                            Wym = P::normal_velocity(fm[1], 1);
-                            Wyp = P::normal_velocity(fpv[1], 1);
-                            if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
-                    phim[c1] = re[P::R_PHI * R2 + c2];
+                for (int f = 0; f < NF; ++f) {
+                    const T* F = fpi + f * R1;
+                    const T fc = F[own_c1];
+                    const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
+                    const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
+                    out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
+                    acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
+                    fprev[f] = fc;
                 }
             }
-            __syncthreads();
-            // ---- phase 2: Lagrangian fluxes of the own tile cell (plane e) -----
-            if (active && own_tile) {
-                const T Wzm = wz_prev;
-                // upwind cell of each lateral face (the own cell where the face
-                // velocity points away from it)
-                const int cxm = own_c1 - (Wxm > T(0) ? 1 : 0);
-                const int cxp = own_c1 + (Wxp > T(0) ? 0 : 1);
-                const int cym = own_c1 - (Wym > T(0) ? W1 : 0);
-                const int cyp = own_c1 + (Wyp > T(0) ? 0 : W1);
-                T out[NF];
-                if constexpr (PK) {
-                    // fields in pairs with packed float32 arithmetic (one instruction
-                    // for two fields); the same operations as the scalar form below
-                    const float2 wz = make_float2(Wzm, Wzm), nr = make_float2(-rat, -rat), pr = make_float2(rat, rat);
-                    const float2 wxp = make_float2(Wxp, Wxp), nwxm = make_float2(-Wxm, -Wxm);
-                    const float2 wyp = make_float2(Wyp, Wyp), nwym = make_float2(-Wym, -Wym);
-                    const bool zup = Wzm > T(0);
+            const int l = e - 1;
+            if (l >= z0 && l < z1 && own_valid) {
+                P::finish(out, gamma, eta, q, vmax, bad);
+                const size_t g = size_t(l) * plane + own_g;
 #pragma unroll
-                    for (int f = 0; f < NF; f += 2) {
-                        float2 fc, uxm, uxp, uym, uyp;
-                        if constexpr (FP2) {
-                            const float2* F2 = reinterpret_cast<const float2*>(fpb) + (f / 2) * R1;
-                            fc = F2[own_c1];
-                            uxm = F2[cxm];
-                            uxp = F2[cxp];
-                            uym = F2[cym];
-                            uyp = F2[cyp];
-                        } else {
-                            const T* F0 = fpb + f * R1;
-                            const T* F1 = F0 + R1;
-                            fc = make_float2(F0[own_c1], F1[own_c1]);
-                            uxm = make_float2(F0[cxm], F1[cxm]);
-                            uxp = make_float2(F0[cxp], F1[cxp]);
-                            uym = make_float2(F0[cym], F1[cym]);
-                            uyp = make_float2(F0[cyp], F1[cyp]);
-                        }
-                        const float2 Fzm = __fmul2_rn(wz, zup ? make_float2(fprev[f], fprev[f + 1]) : fc);
-                        const float2 o = __ffma2_rn(nr, Fzm, make_float2(acc[f], acc[f + 1]));   // completes plane e-1
-                        float2 t = __fadd2_rn(__ffma2_rn(nwxm, uxm, __fmul2_rn(wxp, uxp)),
-                                              __ffma2_rn(nwym, uym, __fmul2_rn(wyp, uyp)));
-                        const float2 n2 = __ffma2_rn(pr, Fzm, __ffma2_rn(nr, t, fc));
-                        out[f] = o.x;
-                        out[f + 1] = o.y;
-                        acc[f] = n2.x;
-                        acc[f + 1] = n2.y;
-                        fprev[f] = fc.x;
-                        fprev[f + 1] = fc.y;
-                    }
+                for (int f = 0; f < NF; ++f) __stcs(a.out + f * a.fs + g, out[f]);   // streaming global store
+            }
+        };
+
+        issue_plane(z0 - 2);
+        issue_plane(z0 - 1);
+        if constexpr (!C::DB) {
+            // Two barriers per plane.  Iteration e:
+            //   [copies of planes e, e+1 landed; barrier]
+            //   phase 1: z faces e+1/2 and the Eulerian update of plane e over R1 (S2)
+            //   [barrier]
+            //   phase 2: Lagrangian fluxes of the own cell at plane e (S3), then the x/y
+            //            faces of plane e+1 (S1) -- the own cell's face velocities were
+            //            kept in registers in phase 1, so the face buffers can be reused
+            for (int e = z0 - 2; e <= z1; ++e) {
+                // plane e + 2 goes into the slot of plane e - 1 (last read in phase 1
+                // of the previous iteration); the staged extra fields of plane e + 1
+                // (read in phase 1 of the next iteration) travel in the same group
+                if (e + 2 <= z1 + 1) {
+                    if (SEX && NEX > 0 && e + 1 >= z0 - 1) issue_extra(e + 1);
+                    issue_plane(e + 2);
+                    cp_async_wait<1>();
                 } else {
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        const T* F = fpb + f * R1;
-                        const T fc = F[own_c1];
-                        const T uxm = F[cxm], uxp = F[cxp], uym = F[cym], uyp = F[cyp];
-                        const T Fzm = Wzm * (Wzm > T(0) ? fprev[f] : fc);
-                        out[f] = acc[f] - rat * Fzm;                           // completes plane e-1
-                        acc[f] = fc - rat * ((Wxp * uxp - Wxm * uxm) + (Wyp * uyp - Wym * uym)) + rat * Fzm;
-                        fprev[f] = fc;
-                    }
+                    cp_async_wait<0>();
                 }
-                const int l = e - 1;
-                if (l >= z0 && l < z1 && own_valid) {
-                    P::finish(out, gamma, eta, q, vmax, bad);
-                    const size_t g = size_t(l) * plane + own_g;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) __stcs(a.out + f * a.fs + g, out[f]);   // streaming global store
-                }
+                __syncthreads();
+                phase1(e);
+                __syncthreads();
+                if (e >= z0 - 1 && own_tile) s3(e);
+                if (e + 1 <= z1) xy_faces(ring + ring_slot(e + 1) * NR * R2, e + 1);
             }
-            // ---- phase 2: x/y faces of plane e + 1 ----------------------------
-            if (e + 1 <= z1) xy_faces(rp);
+        } else {
+            // One barrier per plane (f' and the x/y faces double-buffered by plane
+            // parity).  Iteration e, after the barrier that follows the landing of
+            // planes e and e+1:
+            //   copies of plane e+2 into the slot of plane e-1 (last read before it);
+            //   S3 of plane e-1 from f'_{e-1} (complete at the barrier), with the
+            //   face velocities phase 1 of plane e-1 left in registers;
+            //   phase 1 of plane e: f'_e into the other buffer, reading the x/y
+            //   faces of plane e (written in the previous iteration);
+            //   x/y faces of plane e+1 into the buffer last read by phase 1 of
+            //   plane e-1.
+            for (int e = z0 - 2; e <= z1 + 1; ++e) {
+                cp_async_wait<0>();
+                __syncthreads();
+                if (e + 2 <= z1 + 1) issue_plane(e + 2);
+                if (e - 1 >= z0 - 1 && own_tile) s3(e - 1);
+                if (e <= z1) phase1(e);
+                if (e + 1 <= z1) xy_faces(ring + ring_slot(e + 1) * NR * R2, e + 1);
+            }
         }
         cp_async_wait<0>();
         // next segment (balanced split only)

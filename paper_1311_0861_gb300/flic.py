@@ -32,7 +32,9 @@ EXPORTS = ("flic_init_grid", "flic_set_state", "flic_set_state_device", "flic_ge
            "flic_get_state_device", "flic_step", "flic_run", "flic_solve_poisson",
            "flic_step_diagnostics", "flic_diagnostics", "flic_sync", "flic_destroy",
            "flic_last_error", "flic_version", "flic_profile", "flic_launches_per_step",
-           "flic_state_diagnostics_noalloc",
+           "flic_state_diagnostics_noalloc", "flic_autotune", "flic_num_tile_configs", "flic_set_tile_config",
+           "flic_tile_config", "flic_ensemble_autotune", "flic_ensemble_num_tile_configs", "flic_ensemble_set_tile_config",
+           "flic_ensemble_tile_config",
            "flic_ensemble_create", "flic_ensemble_set_state", "flic_ensemble_get_state", "flic_ensemble_step",
            "flic_ensemble_diagnostics", "flic_ensemble_profile", "flic_ensemble_launches_per_step",
            "flic_ensemble_destroy", "flic_ensemble_last_error")
@@ -103,6 +105,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.flic_ensemble_last_error.restype = ctypes.c_char_p
     lib.flic_state_diagnostics_noalloc.argtypes = [ctypes.POINTER(P), P, ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_double, P, ctypes.POINTER(Diag)]
+    IP = ctypes.POINTER(ctypes.c_int)
+    DP = ctypes.POINTER(ctypes.c_double)
+    lib.flic_autotune.argtypes = [P, ctypes.c_int, ctypes.c_int, DP]
+    lib.flic_num_tile_configs.argtypes = [P, IP, IP]
+    lib.flic_set_tile_config.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.flic_tile_config.argtypes = [P, IP, IP, ctypes.c_char_p, ctypes.c_int]
+    lib.flic_ensemble_autotune.argtypes = [P, ctypes.c_int, DP]
+    lib.flic_ensemble_num_tile_configs.argtypes = [P, IP, IP]
+    lib.flic_ensemble_set_tile_config.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.flic_ensemble_tile_config.argtypes = [P, IP, IP, IP, IP, ctypes.c_char_p, ctypes.c_int]
     lib.flic_step_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
     lib.flic_diagnostics.argtypes = [P, ctypes.POINTER(Diag)]
     lib.flic_sync.argtypes = [P]
@@ -256,6 +268,36 @@ class Grid:
             raise FlicError(rc, self.lib.flic_last_error(self._h).decode())
         return rc
 
+    # -- launch-shape tuner ---------------------------------------------------------
+    def num_tile_configs(self):
+        """(number of compiled gas-kernel shapes, number of moment-kernel shapes)."""
+        ng, nb = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.flic_num_tile_configs(self._h, ctypes.byref(ng), ctypes.byref(nb)))
+        return ng.value, nb.value
+
+    def set_tile_config(self, gas: int = -1, bme: int = -1):
+        self._check(self.lib.flic_set_tile_config(self._h, int(gas), int(bme)))
+
+    def tile_config(self) -> dict:
+        """{"gas": index, "bme": index, "text": description} of the shapes in use."""
+        g, b = ctypes.c_int(), ctypes.c_int()
+        buf = ctypes.create_string_buffer(512)
+        self._check(self.lib.flic_tile_config(self._h, ctypes.byref(g), ctypes.byref(b), buf, len(buf)))
+        return {"gas": g.value, "bme": b.value, "text": buf.value.decode()}
+
+    def autotune(self, reps: int = 5, use_cache: bool = True) -> dict:
+        """Times every compiled shape of both fluid kernels on the current state and
+        keeps the fastest; returns {"cached": bool, "ms_gas": [...], "ms_bme": [...]}
+        (the lists are empty when a cached choice was applied)."""
+        ng, nb = self.num_tile_configs()
+        ms = (ctypes.c_double * (ng + nb))()
+        rc = self.lib.flic_autotune(self._h, int(reps), int(bool(use_cache)), ms)
+        if rc < 0:
+            self._check(rc)
+        if rc == 1:
+            return {"cached": True, "ms_gas": [], "ms_bme": []}
+        return {"cached": False, "ms_gas": list(ms)[:ng], "ms_bme": list(ms)[ng:]}
+
     def solve_poisson(self, want=True):
         if not want:
             self._check(self.lib.flic_solve_poisson(self._h, None))
@@ -366,6 +408,34 @@ class Ensemble:
 
     def launches_per_step(self) -> int:
         return self._check(self.lib.flic_ensemble_launches_per_step(self._e))
+
+    def num_tile_configs(self):
+        ng, nb = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.flic_ensemble_num_tile_configs(self._e, ctypes.byref(ng), ctypes.byref(nb)))
+        return ng.value, nb.value
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Times every (compiled shape, z-chunk cap 16/32/64) of both fluid kernels
+        over the work list and keeps the fastest of each; returns the mean ms per
+        launch as {"ms_gas": [[cap16, cap32, cap64] per shape], "ms_bme": [...]}
+        (-1: skipped)."""
+        ng, nb = self.num_tile_configs()
+        ms = (ctypes.c_double * (3 * (ng + nb)))()
+        self._check(self.lib.flic_ensemble_autotune(self._e, int(reps), ms))
+        v = list(ms)
+        rows = [v[3 * i:3 * i + 3] for i in range(ng + nb)]
+        return {"ms_gas": rows[:ng], "ms_bme": rows[ng:]}
+
+    def set_tile_config(self, gas: int = -1, bme: int = -1, tz_gas: int = -1, tz_bme: int = -1):
+        self._check(self.lib.flic_ensemble_set_tile_config(self._e, int(gas), int(bme), int(tz_gas), int(tz_bme)))
+
+    def tile_config(self) -> dict:
+        g, b, tg, tb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        buf = ctypes.create_string_buffer(512)
+        self._check(self.lib.flic_ensemble_tile_config(self._e, ctypes.byref(g), ctypes.byref(b), ctypes.byref(tg),
+                                                       ctypes.byref(tb), buf, len(buf)))
+        return {"gas": g.value, "bme": b.value, "tz_gas": tg.value, "tz_bme": tb.value, "text": buf.value.decode()}
+
 
     def close(self):
         if getattr(self, "_e", None) and self._e.value:

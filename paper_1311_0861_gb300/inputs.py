@@ -120,6 +120,38 @@ def sphere(N: int = 32, seed: int = 1, gamma: float = 5.0 / 3.0) -> Setup:
 
 
 # ---------------------------------------------------------------------------
+# the paper's cloud collision test (Sec. 4.5)
+# ---------------------------------------------------------------------------
+def cloud_collision(N: int = 32, half_width: float = 2.5, separation: float = 2.4, v_collide: float = 1.0,
+                    gamma: float = 5.0 / 3.0) -> Setup:
+    """Two copies of the hydrostatic gas sphere of Sec. 4.5 (rho = 1 - r inside
+    r = 1 with the printed pressure p0(r) = -pi r^2 (9 r^2 - 28 r + 24)/36 + 5 pi/36,
+    G = 1) centred at x = -+separation/2, approaching along x at relative speed
+    v_collide (each at +-v_collide/2); background rho = 1e-3, p = 1e-5, moving
+    with the nearer cloud.  The collisionless component is a cold passive tracer
+    (n = 1e-6, Pi = 1e-12 I) with the gas velocity.  The box is
+    [-half_width, half_width]^3 (isolated gravity and outflow boundaries are the
+    intended settings)."""
+    h = 2.0 * half_width / N
+    c = -half_width + (np.arange(N) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rho = np.full(x.shape, 1e-3)
+    p = np.full(x.shape, 1e-5)
+    for cx in (-0.5 * separation, 0.5 * separation):
+        r = np.sqrt((x - cx) ** 2 + y * y + z * z)
+        inside = r <= 1.0
+        p0 = -np.pi * r * r * (9.0 * r * r - 28.0 * r + 24.0) / 36.0 + 5.0 * np.pi / 36.0
+        rho = np.where(inside, np.maximum(1.0 - r, 1e-3), rho)
+        p = np.where(inside, np.maximum(p0, 1e-5), p)
+    vx = np.where(x < 0.0, 0.5 * v_collide, -0.5 * v_collide)
+    zero = np.zeros_like(rho)
+    n = np.full(x.shape, 1e-6)
+    P = {"xx": 1e-12 + zero, "yy": 1e-12 + zero, "zz": 1e-12 + zero, "xy": zero, "xz": zero, "yz": zero}
+    st = _finish(rho, rho * vx, zero, zero, p, n, n * vx, zero, zero, P, gamma)
+    return Setup(st, h, gamma, poisson="isolated", name=f"cloud-collision-{N}^3")
+
+
+# ---------------------------------------------------------------------------
 # galaxy pieces
 # ---------------------------------------------------------------------------
 def _rot_y(theta):

@@ -1,0 +1,140 @@
+"""The launch-shape tuner and every compiled launch shape of the fluid kernels.
+
+Each fluid kernel is compiled in several shapes (tile, threads per block, blocks
+per SM) used with a z split; all must compute the step of Sec. 2.1-2.4:
+  * every shape, FP64, periodic and outflow: one step equals the oracle to 1e-11
+    of each field's max (N = 24: one ragged tile column; N = 48: several tiles
+    with ragged edges for every tile width and height);
+  * every shape, float32: equals the oracle to 2e-5 of each field's max;
+  * the tuner's choice is the fastest shape it timed, a second call reuses the
+    cached choice, and the tuned step (also as a CUDA-graph replay) equals the
+    oracle;
+  * ensembles: every (shape, chunk cap) keeps each run equal to the run stepped
+    alone, and the ensemble tuner's choice too.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1311_0861_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+FIELDS = O.FIELDS
+
+
+@pytest.fixture(scope="module")
+def flic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_0861_gb300 import flic as F
+    if not os.path.exists(F.LIB_PATH):
+        from paper_1311_0861_gb300 import build
+        build.build()
+    F.load()
+    return F
+
+
+def max_rel(a, b):
+    return {f: float(np.max(np.abs(a[f] - b[f])) / max(1e-300, np.max(np.abs(b[f])))) for f in FIELDS}
+
+
+def shape_counts(F, precision):
+    with F.Grid(16, precision=precision) as g:
+        return g.num_tile_configs()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+@pytest.mark.parametrize("N,boundary", [(24, "periodic"), (48, "periodic"), (24, "outflow")])
+def test_every_shape_matches_oracle(flic, precision, tol, N, boundary):
+    s = I.random_state((N, N, N), seed=500 + N, rough=True)
+    prm = O.Params(h=s.h, gamma=s.gamma, boundary=boundary)
+    ref, rec = O.step(s.state, prm)
+    ng, nb = shape_counts(flic, precision)
+    pairs = [(k, min(k, nb - 1)) for k in range(ng)] + [(0, k) for k in range(nb)]
+    for gas, bme in pairs:
+        with flic.Grid(N, precision=precision, gamma=s.gamma, boundary=boundary, box=(-1.0, -1.0 + N * s.h)) as g:
+            g.set_tile_config(gas, bme)
+            assert g.tile_config()["gas"] == gas and g.tile_config()["bme"] == bme
+            g.set_state(s.state)
+            g.step()
+            out = g.get_state()
+            d = g.step_diagnostics()
+        err = max_rel(out, ref)
+        assert max(err.values()) <= tol, (gas, bme, err)
+        assert abs(d["mass_gas"] - rec["mass_gas"]) <= 1e-6 * rec["mass_gas"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_choice_cache_and_parity(flic, precision):
+    N = 48
+    s = I.head_on(N)
+    prm = O.Params(h=s.h, gamma=s.gamma)
+    ref, _ = O.run(s.state, prm, 3)
+    with flic.Grid(N, precision=precision, gamma=s.gamma) as g:
+        g.set_state(s.state)
+        t = g.autotune(reps=3, use_cache=False)
+        ng, nb = g.num_tile_configs()
+        assert not t["cached"] and len(t["ms_gas"]) == ng and len(t["ms_bme"]) == nb
+        cfg = g.tile_config()
+        timed_g = [(m, i) for i, m in enumerate(t["ms_gas"]) if m >= 0]
+        timed_b = [(m, i) for i, m in enumerate(t["ms_bme"]) if m >= 0]
+        assert cfg["gas"] == min(timed_g)[1] and cfg["bme"] == min(timed_b)[1]
+        assert cfg["text"].startswith("gas: ")
+        # tuning leaves the state untouched; the tuned steps (graph replay) match the oracle
+        g.run(3)
+        out = g.get_state()
+        assert g.step_diagnostics()["step"] == 3
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    err = {f: float(np.sum(np.abs(out[f] - ref[f])) / max(1e-300, np.sum(np.abs(ref[f])))) for f in FIELDS}
+    worst = max(err.values()) if precision == "fp64" else max(err["rho"], err["n"])
+    assert worst <= tol, err
+    with flic.Grid(N, precision=precision, gamma=s.gamma) as g2:
+        g2.set_state(s.state)
+        assert g2.autotune(reps=3)["cached"]
+        assert g2.tile_config()["gas"] == cfg["gas"] and g2.tile_config()["bme"] == cfg["bme"]
+
+
+def test_set_tile_config_rejects_bad_index(flic):
+    with flic.Grid(16) as g:
+        ng, nb = g.num_tile_configs()
+        with pytest.raises(flic.FlicError) as ei:
+            g.set_tile_config(ng, 0)
+        assert ei.value.code == flic.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_shapes_and_tuner(flic, precision):
+    sizes = [16, 24, 32, 12]
+    sts = [I.random_state((n, n, n), seed=600 + i, box=2.0) for i, n in enumerate(sizes)]
+    refs = []
+    for n, s in zip(sizes, sts):
+        with flic.Grid(n, precision=precision) as g:
+            g.set_state(s.state)
+            g.run(2)
+            refs.append(g.get_state())
+    with flic.Ensemble(sizes, precision=precision) as ens:
+        ng, nb = ens.num_tile_configs()
+        trials = [(k, 0, 32, 32) for k in range(ng)] + [(0, k, 16, 64) for k in range(nb)]
+        for gas, bme, tzg, tzb in trials:
+            ens.set_tile_config(gas, bme, tzg, tzb)
+            for r, s in enumerate(sts):
+                ens.set_state(r, s.state)
+            ens.step(2)
+            for r in range(len(sizes)):
+                out = ens.get_state(r)
+                err = max_rel(out, refs[r])
+                tol = 1e-13 if precision == "fp64" else 1e-6
+                assert max(err.values()) <= tol, (gas, bme, r, err)
+        for r, s in enumerate(sts):
+            ens.set_state(r, s.state)
+        t = ens.autotune(reps=2)
+        assert len(t["ms_gas"]) == ng and len(t["ms_bme"]) == nb
+        cfg = ens.tile_config()
+        assert 0 <= cfg["gas"] < ng and 0 <= cfg["bme"] < nb and cfg["tz_gas"] in (16, 32, 64)
+        ens.step(2)
+        for r in range(len(sizes)):
+            err = max_rel(ens.get_state(r), refs[r])
+            assert max(err.values()) <= (1e-13 if precision == "fp64" else 1e-6), (r, err)

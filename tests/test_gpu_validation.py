@@ -257,3 +257,71 @@ def test_acoustic_pulse_leaves_outflow_box(flic):
     out, _ = gpu_run_to(flic, to_cube(st1, N), N, (0.0, 1.0), g, t_end, boundary="outflow")
     check_rows(out, ref, 1e-10, floor=rho0 * c0 * eps)   # the momentum has left with the pulse
     assert np.max(np.abs(out["rho"] - rho0)) < 0.03 * rho0 * eps
+
+
+def test_cloud_collision_isolated_outflow(flic):
+    """The cloud collision of Sec. 4.5 (two rho = 1 - r clouds, L0 = 2.4, v = 1) with
+    isolated gravity and outflow boundaries: the GPU run equals the oracle's
+    (FP64 1e-10, float32 1e-4 in the densities), and each step's mass change equals
+    the closed-form flux through the boundary (test_oracle_cloud_collision.py)."""
+    from paper_1311_0861_gb300 import inputs as I
+    for N in (32, 48):
+        s = I.cloud_collision(N)
+        L = 0.5 * N * s.h
+        prm = O.Params(h=s.h, gamma=s.gamma, poisson="isolated", boundary="outflow")
+        ref, rrec = O.run(s.state, prm, 5)
+        for precision in ("fp64", "mixed"):
+            with flic.Grid(N, precision=precision, gamma=s.gamma, poisson="isolated", boundary="outflow",
+                           box=(-L, L)) as g:
+                g.set_state(s.state)
+                m0 = g.diagnostics()["mass_gas"]
+                dt0 = g.step()
+                m1 = g.diagnostics()["mass_gas"]
+                for _ in range(4):
+                    g.step()
+                out = g.get_state()
+            if precision == "fp64":
+                st = s.state
+                flux = (np.sum(st["mx"][:, :, -1]) - np.sum(st["mx"][:, :, 0]) + np.sum(st["my"][:, -1, :])
+                        - np.sum(st["my"][:, 0, :]) + np.sum(st["mz"][-1, :, :]) - np.sum(st["mz"][0, :, :]))
+                assert abs((m1 - m0) + dt0 * s.h ** 2 * flux) <= 1e-12 * m0
+                for f in FIELDS:
+                    if np.max(np.abs(ref[f])) > 1e-9:
+                        assert rel_l1(out[f], ref[f]) <= 1e-10, (N, f)
+            else:
+                assert rel_l1(out["rho"], ref["rho"]) <= 1e-4 and rel_l1(out["n"], ref["n"]) <= 1e-4
+
+
+def rotate_axes(st, k):
+    """The state with the grid and every vector/tensor component rotated k times
+    by x -> y -> z -> x (a profile along x then lies along y for k = 1, z for k = 2)."""
+    from helpers import permute_state
+    for _ in range(k % 3):
+        st = permute_state(st)
+    return st
+
+
+@pytest.mark.parametrize("axis", [1, 2])
+def test_tubes_along_y_and_z(flic, axis):
+    """Godunov tube 1 (Table 2) and the moment-fluid tube (Sec. 4.2) with their
+    profiles along y or z: the z direction is the one the fused kernel marches
+    (its faces live in registers and the plane ring), y the second tile axis.
+    Rotated back, every row equals the oracle's 1D run (FP64 1e-10)."""
+    gold = json.load(open(os.path.join(GOLD, "shock_tubes.json")))
+    test, g = gold["tests"]["1"], gold["gamma"]
+    N = 64
+    x, h, st1 = tube1d(test, N, g)
+    ref, k1 = run_to(O, st1, O.Params(h=h, gamma=g, G=0.0, courant=0.2), test["t"])
+    cube = rotate_axes(to_cube(st1, N), axis)
+    out, k3 = gpu_run_to(flic, cube, N, (0.0, 4.0), g, test["t"])
+    assert k1 == k3
+    check_rows(rotate_axes(out, 3 - axis), ref, 1e-10)
+
+    gb = json.load(open(os.path.join(GOLD, "bme_shock_tube.json")))
+    L, R = gb["left"], gb["right"]
+    in_left = (x < gb["x0"]) | (x >= gb["x0"] + 2.0)
+    gas = {"rho": 1.0, "v": 0.0, "p": 1.0}
+    st1 = tube_state(x, gas, gas, in_left, 5.0 / 3.0, bme=(dict(L), dict(R)))
+    ref, _ = run_to(O, st1, O.Params(h=h, G=0.0, courant=0.2), gb["t"])
+    out, _ = gpu_run_to(flic, rotate_axes(to_cube(st1, N), axis), N, (0.0, 4.0), 5.0 / 3.0, gb["t"])
+    check_rows(rotate_axes(out, 3 - axis), ref, 1e-10)
