@@ -50,6 +50,11 @@ def parse_args(argv=None):
     p.add_argument("--fp64-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true")
+    p.add_argument("--compare-steps", type=int, default=10,
+                   help="steps after which the mixed path is compared with the FP64 path (10 and 200 at 256^3)")
+    p.add_argument("--tiles", default="auto",
+                   help="launch shapes of the fluid kernels: 'auto' (the tuner times every compiled shape) or "
+                        "'G,B' (indices of the gas and moment shapes, e.g. 0,0 for the defaults)")
     return p.parse_args(argv)
 
 
@@ -300,7 +305,14 @@ def run_single(args, rank, world, stream, clocks):
     esz = 4 if args.precision == "mixed" else 8
     g = flic.Grid(N, precision=args.precision, gamma=setup.gamma, poisson=poisson, stream=stream.cuda_stream)
     g.set_state(setup.state)
-    tune = g.autotune(reps=5)
+    if args.tiles == "auto":
+        tune = g.autotune(reps=5)
+        chosen_by = ("cached launch-shape tuner" if tune["cached"] else
+                     "launch-shape tuner (every compiled shape timed on this GPU)")
+    else:
+        gi, bi = (int(v) for v in args.tiles.split(","))
+        g.set_tile_config(gi, bi)
+        chosen_by = f"fixed on the command line ({args.tiles})"
     tiles = g.tile_config()["text"]
     launches = g.launches_per_step()
     clocks.start()
@@ -353,9 +365,12 @@ def run_single(args, rank, world, stream, clocks):
     # ---- float64 path and mixed-vs-float64 accuracy on the same input ----
     compare = None
     if not args.no_compare and args.precision == "mixed":
+        K = args.compare_steps
         g.set_state(setup.state)
-        g.run(10, sync=True)
-        mixed10 = g.get_state()
+        m0 = g.diagnostics()
+        g.run(K, sync=True)
+        m1 = g.diagnostics()
+        mixedK = g.get_state()
         g.close()
         g64 = flic.Grid(N, precision="fp64", gamma=setup.gamma, poisson=poisson, stream=stream.cuda_stream)
         g64.set_state(setup.state)
@@ -364,13 +379,23 @@ def run_single(args, rank, world, stream, clocks):
         st64, tot64 = g64.profile(args.fp64_steps)
         v64 = N ** 3 * args.fp64_steps / (tot64 / 1e3)
         g64.set_state(setup.state)
-        g64.run(10, sync=True)
-        fp6410 = g64.get_state()
+        d0 = g64.diagnostics()
+        g64.run(K, sync=True)
+        d1 = g64.diagnostics()
+        fp64K = g64.get_state()
         g64.close()
-        l1 = {f: float(np.sum(np.abs(mixed10[f] - fp6410[f])) / np.sum(np.abs(fp6410[f]))) for f in flic.FIELDS}
+        l1 = {f: float(np.sum(np.abs(mixedK[f] - fp64K[f])) / np.sum(np.abs(fp64K[f]))) for f in flic.FIELDS}
+
+        def drift(a, b):
+            e_a = a["ekin_gas"] + a["eint_gas"] + a["ekin_bme"] + a["etherm_bme"] + a["epot"]
+            e_b = b["ekin_gas"] + b["eint_gas"] + b["ekin_bme"] + b["etherm_bme"] + b["epot"]
+            return {"mass_gas": (b["mass_gas"] - a["mass_gas"]) / a["mass_gas"],
+                    "mass_bme": (b["mass_bme"] - a["mass_bme"]) / a["mass_bme"],
+                    "energy": (e_b - e_a) / abs(e_a)}
         compare = {"fp64_value": v64 * world, "fp64_ms_per_step": tot64 / args.fp64_steps,
-                   "mixed_over_fp64": value / (v64 * world),
-                   "rel_l1_mixed_vs_fp64_after_10_steps": l1}
+                   "mixed_over_fp64": value / (v64 * world), "steps": K,
+                   f"rel_l1_mixed_vs_fp64_after_{K}_steps": l1,
+                   "drift_mixed": drift(m0, m1), "drift_fp64": drift(d0, d1)}
     else:
         g.close()
 
@@ -390,9 +415,7 @@ def run_single(args, rank, world, stream, clocks):
                                        f"z-planes on one core, scaled to one full step")}}
     line = {"value": value, "ms_per_step": agg["max_s"] * 1e3 / args.steps,
             "config": {"workload": name, "n": N, "precision": args.precision,
-                       "poisson": f"{poisson} FFT", "tiles": tiles,
-                       "tiles_chosen_by": "cached launch-shape tuner" if tune["cached"] else
-                       "launch-shape tuner (every compiled shape timed on this GPU)",
+                       "poisson": f"{poisson} FFT", "tiles": tiles, "tiles_chosen_by": chosen_by,
                        "l2": f"inputs larger than L2 (state {22 * esz * N ** 3 / 2 ** 30:.2f} GiB)"
                        if 22 * esz * N ** 3 > 2 ** 27 else "state smaller than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -87,6 +87,10 @@ typedef struct flic_grid_desc {
     int precision;       /* enum flic_precision */
     int poisson_bc;      /* enum flic_poisson_bc */
     int hydro_bc;        /* enum flic_hydro_bc (0: periodic) */
+    double cooling;      /* Lambda >= 0 of the gas cooling function q of Sec. 2, whose tabulated form the
+                            paper takes from Sutherland & Dopita; here an analytic placeholder
+                            q = Lambda rho^2 sqrt(eps), subtracted (times tau, time-n state) from E and e
+                            in the Eulerian stage; 0 = adiabatic */
 } flic_grid_desc;
 
 /* Per-step record.  Conserved sums describe the state at the START of the step

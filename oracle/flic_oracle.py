@@ -68,7 +68,11 @@ READINGS = {
            "BME takes Pi = nE - q q^T/n when tr >= eta tr(nE) and every diagonal "
            "entry is positive, else resets nE = Pi + q q^T/n; eta = 1e-3.",
     "s12": "Cell centres at box_min + (i + 1/2) h.",
-    "s13": "No cooling (q = 0).",
+    "s13": "No cooling by default (q = 0).  Params.cooling = Lambda > 0 switches on an "
+           "analytic placeholder for the cooling function of the gas energy equations "
+           "(Sec. 2; the paper's tabulated Sutherland-Dopita function is not available): "
+           "q = Lambda rho^2 sqrt(eps) = Lambda rho sqrt(rho e), evaluated on the time-n "
+           "state and subtracted (times tau) from both E and e in the Eulerian stage.",
     "s14": "No floors; non-positive rho, n, e, Pi_dd or a non-finite value flags "
            "the state non-physical.",
     "s15": "kappa_bme sums the 6 independent components of the symmetric tensor.",
@@ -87,6 +91,7 @@ class Params:
     poisson: str = "periodic"  # "periodic" (s5/s6) or "isolated" (s7)
     boundary: str = "periodic" # hydro boundaries: "periodic" or "outflow" (s8)
     flux: str = "A"            # Lagrangian transport velocity: reading "A" or "B" of s1
+    cooling: float = 0.0       # Lambda of the cooling placeholder q = Lambda rho^2 sqrt(eps) (s13)
 
 
 # --------------------------------------------------------------------------
@@ -281,6 +286,11 @@ def advance(st, phi, tau, prm: Params, record=None):
     E1 = (E - r * sum(_delta(P[d] * V[d], d) for d in DIRS)
           - tau * sum(m[d] * gphi[d] for d in DIRS))
     e1 = e - tau * (g - 1.0) * e * sum(_delta(V[d], d) for d in DIRS) / h
+    if prm.cooling != 0.0:
+        # the cooling function -q of both energy equations (Sec. 2), reading s13
+        q = prm.cooling * rho * np.sqrt(rho * e)
+        E1 = E1 - tau * q
+        e1 = e1 - tau * q
     gas1 = {"rho": rho, "mx": m1["x"], "my": m1["y"], "mz": m1["z"], "E": E1, "e": e1}
 
     # ---------------- Boltzmann moments, Sec. 2.2 ----------------

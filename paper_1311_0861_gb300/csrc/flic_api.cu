@@ -105,6 +105,7 @@ static StencilArgs<T> fluid_args(const flic_handle* h, int fluid, const StepCfg&
     a.inv_h = 1.0 / h->h;
     a.gamma = T(h->d.gamma);
     a.eta = T(h->d.eta);
+    a.cool = T(h->d.cooling);
     a.vmax = h->scal + S_VMAX_NEXT;
     a.status = h->status;
     const int f0 = fluid == FLUID_GAS ? F_RHO : F_N;   // gas: fields 0..5; moments: 6..21
@@ -413,7 +414,7 @@ int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out) 
     *out = nullptr;
     if (!valid_n(desc->n)) { g_init_err = "n must be 2^a 3^b, a multiple of 4, 8 <= n <= 1024"; return FLIC_ERR_INVALID_ARG; }
     if (!(desc->box_max > desc->box_min) || !(desc->gamma > 1.0) || !(desc->courant > 0.0) ||
-        !(desc->eta >= 0.0) || !(desc->G >= 0.0)) {
+        !(desc->eta >= 0.0) || !(desc->G >= 0.0) || !(desc->cooling >= 0.0)) {
         g_init_err = "invalid physical constants";
         return FLIC_ERR_INVALID_ARG;
     }

@@ -115,11 +115,12 @@ int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
     if (ev) ENS_CK(e, cudaEventRecord(ev[1], e->st));
     ENS_CK(e, stencil_launch_batch<T>(FLUID_GAS, e->cand[FLUID_GAS],
                                       reinterpret_cast<const StencilArgs<T>*>(e->tab_gas[e->cur]), e->work_gas,
-                                      e->nwork_gas, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
+                                      e->nwork_gas, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->d.cooling != 0.0,
+                                      e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[2], e->st));
     ENS_CK(e, stencil_launch_batch<T>(FLUID_BME, e->cand[FLUID_BME],
                                       reinterpret_cast<const StencilArgs<T>*>(e->tab_bme[e->cur]), e->work_bme,
-                                      e->nwork_bme, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, e->st));
+                                      e->nwork_bme, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, false, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[3], e->st));
     ENS_CK(e, step_finalize_batch(e->fin_tab, e->nruns, 1, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[4], e->st));
@@ -227,6 +228,7 @@ int ens_build_work(flic_ensemble* e) {
             a.inv_h = 1.0 / c.h;
             a.gamma = T(e->d.gamma);
             a.eta = T(e->d.eta);
+            a.cool = T(e->d.cooling);
             a.vmax = sc + S_VMAX_NEXT;
             a.status = e->status + r;
             StencilArgs<T> g = a, b = a;
@@ -397,10 +399,11 @@ int ens_tune(flic_ensemble* e, int reps, double* ms) {
                 const WorkItem* work = gas ? e->work_gas : e->work_bme;
                 const int nwork = gas ? e->nwork_gas : e->nwork_bme;
                 const bool out = e->d.hydro_bc == FLIC_HYDRO_OUTFLOW;
-                cudaError_t er = stencil_launch_batch<T>(fluid, c, tab, work, nwork, out, e->st);
+                const bool cool = gas && e->d.cooling != 0.0;
+                cudaError_t er = stencil_launch_batch<T>(fluid, c, tab, work, nwork, out, cool, e->st);
                 if (er == cudaSuccess) er = cudaEventRecord(e0, e->st);
                 for (int r = 0; r < reps && er == cudaSuccess; ++r)
-                    er = stencil_launch_batch<T>(fluid, c, tab, work, nwork, out, e->st);
+                    er = stencil_launch_batch<T>(fluid, c, tab, work, nwork, out, cool, e->st);
                 if (er == cudaSuccess) er = cudaEventRecord(e1, e->st);
                 if (er == cudaSuccess) er = cudaEventSynchronize(e1);
                 float el = 0.f;
@@ -495,7 +498,8 @@ int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, f
         const flic_grid_desc& d = descs[r];
         if (d.precision != d0.precision || d.poisson_bc != d0.poisson_bc || d.hydro_bc != d0.hydro_bc ||
             d.gamma != d0.gamma || d.G != d0.G ||
-            d.courant != d0.courant || d.eta != d0.eta || d.box_min != d0.box_min || d.box_max != d0.box_max) {
+            d.courant != d0.courant || d.eta != d0.eta || d.box_min != d0.box_min || d.box_max != d0.box_max ||
+            d.cooling != d0.cooling) {
             set_global_error("ensemble runs must share every constant except n");
             return FLIC_ERR_INVALID_ARG;
         }
@@ -508,6 +512,7 @@ int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, f
         }
     }
     if (!(d0.box_max > d0.box_min) || !(d0.gamma > 1.0) || !(d0.courant > 0.0) || !(d0.G >= 0.0) ||
+        !(d0.cooling >= 0.0) ||
         (d0.precision != FLIC_FP64 && d0.precision != FLIC_MIXED) ||
         (d0.poisson_bc != FLIC_PERIODIC && d0.poisson_bc != FLIC_ISOLATED) ||
         (d0.hydro_bc != FLIC_HYDRO_PERIODIC && d0.hydro_bc != FLIC_HYDRO_OUTFLOW)) {

@@ -39,7 +39,7 @@ struct StencilCand {
     cudaError_t (*prepare)();
     cudaError_t (*launch)(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st);
     cudaError_t (*launch_batch)(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
-                                cudaStream_t st);
+                                bool cool, cudaStream_t st);
 };
 template <typename T> const StencilCand<T>* gas_cands(int* count);
 template <typename T> const StencilCand<T>* bme_cands(int* count);
@@ -55,7 +55,7 @@ template <typename T> cudaError_t stencil_launch(int fluid, const StencilArgs<T>
 // One launch over a work list spanning several runs (table and work in device memory).
 template <typename T>
 cudaError_t stencil_launch_batch(int fluid, int cand, const StencilArgs<T>* table, const WorkItem* work, int nwork,
-                                 bool outflow, cudaStream_t st);
+                                 bool outflow, bool cool, cudaStream_t st);
 
 // float64 <-> storage precision conversion of one field.
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);

@@ -35,11 +35,11 @@ cudaError_t stencil_launch(int fluid, const StencilArgs<T>& a, const StepCfg& c,
 
 template <typename T>
 cudaError_t stencil_launch_batch(int fluid, int cand, const StencilArgs<T>* table, const WorkItem* work, int nwork,
-                                 bool outflow, cudaStream_t st) {
+                                 bool outflow, bool cool, cudaStream_t st) {
     int n = 0;
     const StencilCand<T>* t = stencil_cands<T>(fluid, &n);
     if (cand < 0 || cand >= n) return cudaErrorInvalidValue;
-    return t[cand].launch_batch(table, work, nwork, outflow, st);
+    return t[cand].launch_batch(table, work, nwork, outflow, cool, st);
 }
 
 template cudaError_t stencil_prepare<float>();
@@ -49,8 +49,8 @@ template StepCfg stencil_cfg<double>(int, int, int, int);
 template cudaError_t stencil_launch<float>(int, const StencilArgs<float>&, const StepCfg&, cudaStream_t);
 template cudaError_t stencil_launch<double>(int, const StencilArgs<double>&, const StepCfg&, cudaStream_t);
 template cudaError_t stencil_launch_batch<float>(int, int, const StencilArgs<float>*, const WorkItem*, int, bool,
-                                                 cudaStream_t);
+                                                 bool, cudaStream_t);
 template cudaError_t stencil_launch_batch<double>(int, int, const StencilArgs<double>*, const WorkItem*, int, bool,
-                                                  cudaStream_t);
+                                                  bool, cudaStream_t);
 
 }  // namespace flic

@@ -56,6 +56,7 @@ struct StencilArgs {
     const double* tau;        // step size (device scalar)
     double inv_h;             // 1 / h
     T gamma, eta;
+    T cool;                   // Lambda of the gas cooling placeholder (0: adiabatic)
     double* partials;         // [num_blocks][Q_COUNT] per-block sums (unscaled by h^3)
     double* vmax;             // signal speed of the output state (atomic max)
     unsigned int* status;     // ST_* bits
@@ -121,6 +122,7 @@ struct GasPhys {
     static constexpr int NFACE = 2;   // V, P
     static constexpr int R_PHI = 6;
     static constexpr int NQ = 8;      // accumulated quantities
+    static constexpr bool COOLS = true;   // has the cooling term (instances with and without it)
     static __device__ __forceinline__ int ring_field(int r) { return r; }
     static __device__ __forceinline__ int extra_field(int) { return 0; }
 
@@ -144,7 +146,7 @@ struct GasPhys {
     // faces; g[d]: central-difference gradient of Phi.
     static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
                                                  const T fpv[3][NFACE], const T g[3], T tau,
-                                                 T rat, T gamma, const T*, T* f1) {
+                                                 T rat, T gamma, T cool, const T*, T* f1) {
         T rho = r[0 * R2 + c];
         T m[3] = {r[1 * R2 + c], r[2 * R2 + c], r[3 * R2 + c]};
         T E = r[4 * R2 + c], e = r[5 * R2 + c];
@@ -160,6 +162,12 @@ struct GasPhys {
         for (int d = 0; d < 3; ++d) f1[1 + d] = m[d] - rat * (fpv[d][1] - fm[d][1]) - tau * rho * g[d];
         f1[4] = E - rat * dPV - tau * mg;
         f1[5] = e - rat * (gamma - T(1)) * e * dV;
+        if (cool != T(0)) {
+            // cooling placeholder q = Lambda rho^2 sqrt(e / rho) of both energy equations
+            const T qc = cool * rho * sqr_root(rho * e);
+            f1[4] -= tau * qc;
+            f1[5] -= tau * qc;
+        }
     }
 
     static __device__ __forceinline__ T normal_velocity(const T* facev, int) { return facev[0]; }
@@ -213,6 +221,7 @@ struct BmePhys {
     static constexpr int NFACE = 6;   // u*_x, u*_y, u*_z, Pi*_xd, Pi*_yd, Pi*_zd
     static constexpr int R_P = 4, R_PHI = 10;
     static constexpr int NQ = 8;
+    static constexpr bool COOLS = false;
     static __device__ __forceinline__ int ring_field(int r) { return r < 4 ? r : r + 6; }
     static __device__ __forceinline__ int extra_field(int k) { return 4 + k; }
 
@@ -278,7 +287,7 @@ struct BmePhys {
     // nE: the cell's energy tensor (6 components, read directly from global memory)
     static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
                                                  const T fpv[3][NFACE], const T g[3], T tau,
-                                                 T rat, T, const T* nE, T* f1) {
+                                                 T rat, T, T, const T* nE, T* f1) {
         T n = r[0 * R2 + c];
         T q[3] = {r[1 * R2 + c], r[2 * R2 + c], r[3 * R2 + c]};
         T Pi[6];
@@ -381,10 +390,11 @@ constexpr int RING_SLOTS = 3;   // planes e, e+1 in use, e+2 in flight
 // are split over blocks is chosen at launch (StepCfg).
 // With DB the transported state f' and the x/y face buffers are double-buffered
 // by plane parity, which lets one barrier per plane separate the stages (see
-// the kernel).
-template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_, bool DB_ = false>
+// the kernel).  PAIRS: float32 f' stored as field pairs (8-byte shared loads and
+// stores) -- 1 on, 0 off, -1 for the fluid's default (on for the gas).
+template <int TX_, int TY_, int MINB_, bool SEX_, bool WIDE_, int HR_, bool DB_ = false, int PAIRS_ = -1>
 struct TileCfg {
-    static constexpr int TX = TX_, TY = TY_, MINB = MINB_, HR = HR_;
+    static constexpr int TX = TX_, TY = TY_, MINB = MINB_, HR = HR_, PAIRS = PAIRS_;
     static constexpr bool SEX = SEX_, WIDE = WIDE_, DB = DB_;
 };
 
@@ -478,12 +488,15 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ int ring_slot(int p) { return ((p % RING_SLOTS) + RING_SLOTS) % RING_SLOTS; }
+// Ring slot of plane p (p >= -2: the march starts two planes below its range).
+__device__ __forceinline__ int ring_slot(int p) { return int(unsigned(p + RING_SLOTS) % unsigned(RING_SLOTS)); }
 
 // OUT: outflow hydro boundaries -- indices clamp to the edge instead of
 // wrapping, so the ring holds two layers of ghost copies of the edge cells
 // (zero gradient) and the step acts as on the grid extended by them.
-template <class P, typename T, class C, bool OUT>
+// COOL: the gas cooling placeholder is applied (a separate instance, so the
+// adiabatic kernels carry none of its code).
+template <class P, typename T, class C, bool OUT, bool COOL = false>
 __global__ void __launch_bounds__(Geom<P, T, C>::NTH, C::MINB)
 fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     using Gm = Geom<P, T, C>;
@@ -497,7 +510,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     // kernel the pair layout measured slower (its loads raise register
     // pressure past the 128-register budget), so it keeps scalar rows.
     constexpr bool PK = std::is_same<T, float>::value && P::NF % 2 == 0;
-    constexpr bool FP2 = PK && P::NF < 16;
+    constexpr bool FP2 = PK && (C::PAIRS < 0 ? P::NF < 16 : C::PAIRS > 0);
     static_assert(!FP2 || ((Gm::ring_elems + Gm::xf_elems + Gm::yf_elems + Gm::zc_elems) % 2 == 0 &&
                            Gm::fp_one % 2 == 0),
                   "the f' buffers must start on an 8-byte boundary");
@@ -566,10 +579,21 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     const bool balanced = !batch.work && a.tz <= 0;
     const int N = a.n;
     const size_t plane = size_t(N) * N;
-    const T tau = T(*a.tau);
-    const T rat = T(*a.tau * a.inv_h);
-    const T half_ih = T(0.5 * a.inv_h);
+    // the step's scalars in the storage precision, formed once per block and
+    // kept in shared memory (a re-read is a shared load, not a float64 load,
+    // multiply and conversion)
+    __shared__ T cst[3];
+    if (tid == 0) {
+        cst[0] = T(*a.tau);
+        cst[1] = T(*a.tau * a.inv_h);
+        cst[2] = T(0.5 * a.inv_h);
+    }
+    __syncthreads();
+    const T tau = cst[0];
+    const T rat = cst[1];
+    const T half_ih = cst[2];
     const T gamma = a.gamma, eta = a.eta;
+    const T cool = COOL ? a.cool : T(0);
     Acc<T> q[P::NQ];
     T vmax = T(0);
     bool bad = false;
@@ -784,7 +808,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                     g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
                     g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
                     T f1[NF];
-                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, ex, f1);
+                    P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, cool, ex, f1);
                     if constexpr (FP2) {
                         // field pairs side by side: one 8-byte store per pair
 #pragma unroll

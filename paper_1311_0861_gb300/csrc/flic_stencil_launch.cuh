@@ -57,36 +57,51 @@ struct StencilOps {
         return c;
     }
 
-    static cudaError_t prepare() {
-        cudaError_t e = cudaFuncSetAttribute(fluid_step_kernel<P, T, C, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Geom<P, T, C>::smem_bytes);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(fluid_step_kernel<P, T, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    template <bool OUT, bool COOL>
+    static cudaError_t set_smem() {
+        return cudaFuncSetAttribute(fluid_step_kernel<P, T, C, OUT, COOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Geom<P, T, C>::smem_bytes);
     }
 
-    static cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
-        BatchArgs<T> none{nullptr, nullptr};
-        const dim3 grid = c.balanced > 0 ? dim3(c.balanced) : dim3(c.tiles_x * c.tiles_y, c.blocks_z);
-        if (a.outflow)
-            fluid_step_kernel<P, T, C, true><<<grid, c.threads, c.smem, st>>>(a, none);
+    static cudaError_t prepare() {
+        cudaError_t e = set_smem<false, false>();
+        if (e == cudaSuccess) e = set_smem<true, false>();
+        if constexpr (P::COOLS) {
+            if (e == cudaSuccess) e = set_smem<false, true>();
+            if (e == cudaSuccess) e = set_smem<true, true>();
+        }
+        return e;
+    }
+
+    // the instance for the boundary kind and the cooling switch
+    static cudaError_t go(bool out, bool cool, dim3 grid, int nth, size_t smem, cudaStream_t st,
+                          const StencilArgs<T>& a, BatchArgs<T> b) {
+        if constexpr (P::COOLS) {
+            if (cool) {
+                if (out)
+                    fluid_step_kernel<P, T, C, true, true><<<grid, nth, smem, st>>>(a, b);
+                else
+                    fluid_step_kernel<P, T, C, false, true><<<grid, nth, smem, st>>>(a, b);
+                return cudaGetLastError();
+            }
+        }
+        if (out)
+            fluid_step_kernel<P, T, C, true, false><<<grid, nth, smem, st>>>(a, b);
         else
-            fluid_step_kernel<P, T, C, false><<<grid, c.threads, c.smem, st>>>(a, none);
+            fluid_step_kernel<P, T, C, false, false><<<grid, nth, smem, st>>>(a, b);
         return cudaGetLastError();
     }
 
+    static cudaError_t launch(const StencilArgs<T>& a, const StepCfg& c, cudaStream_t st) {
+        const dim3 grid = c.balanced > 0 ? dim3(c.balanced) : dim3(c.tiles_x * c.tiles_y, c.blocks_z);
+        return go(a.outflow != 0, a.cool != T(0), grid, c.threads, c.smem, st, a, BatchArgs<T>{nullptr, nullptr});
+    }
+
     static cudaError_t launch_batch(const StencilArgs<T>* table, const WorkItem* work, int nwork, bool outflow,
-                                    cudaStream_t st) {
+                                    bool cool, cudaStream_t st) {
         StencilArgs<T> unused{};
-        BatchArgs<T> b{table, work};
-        constexpr int nth = Geom<P, T, C>::NTH;
-        constexpr size_t smem = Geom<P, T, C>::smem_bytes;
-        if (outflow)
-            fluid_step_kernel<P, T, C, true><<<nwork, nth, smem, st>>>(unused, b);
-        else
-            fluid_step_kernel<P, T, C, false><<<nwork, nth, smem, st>>>(unused, b);
-        return cudaGetLastError();
+        return go(outflow, cool, dim3(nwork), Geom<P, T, C>::NTH, Geom<P, T, C>::smem_bytes, st, unused,
+                  BatchArgs<T>{table, work});
     }
 };
 

@@ -46,7 +46,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("box_min", ctypes.c_double), ("box_max", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("G", ctypes.c_double), ("courant", ctypes.c_double),
                 ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("poisson_bc", ctypes.c_int),
-                ("hydro_bc", ctypes.c_int)]
+                ("hydro_bc", ctypes.c_int), ("cooling", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -186,14 +186,14 @@ class Grid:
 
     def __init__(self, n: int, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
                  precision: str = "fp64", poisson: str = "periodic", boundary: str = "periodic",
-                 stream: int = 0):
+                 cooling: float = 0.0, stream: int = 0):
         self.lib = load()
         self.n = int(n)
         self.h = (box[1] - box[0]) / n
         d = GridDesc(int(n), box[0], box[1], gamma, G, courant, eta,
                      {"fp64": FP64, "mixed": MIXED}[precision],
                      {"periodic": PERIODIC, "isolated": ISOLATED}[poisson],
-                     {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary])
+                     {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary], float(cooling))
         self._h = ctypes.c_void_p()
         rc = self.lib.flic_init_grid(ctypes.byref(d), ctypes.c_void_p(stream or None), ctypes.byref(self._h))
         if rc != OK:
@@ -342,13 +342,14 @@ class Ensemble:
 
     def __init__(self, sizes, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
                  precision: str = "mixed", poisson: str = "periodic", boundary: str = "periodic",
-                 stream: int = 0):
+                 cooling: float = 0.0, stream: int = 0):
         self.lib = load()
         self.sizes = [int(n) for n in sizes]
         hb = {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary]
         descs = (GridDesc * len(self.sizes))(*[
             GridDesc(n, box[0], box[1], gamma, G, courant, eta, {"fp64": FP64, "mixed": MIXED}[precision],
-                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson], hb) for n in self.sizes])
+                     {"periodic": PERIODIC, "isolated": ISOLATED}[poisson], hb, float(cooling))
+            for n in self.sizes])
         self._e = ctypes.c_void_p()
         rc = self.lib.flic_ensemble_create(descs, len(self.sizes), ctypes.c_void_p(stream or None),
                                            ctypes.byref(self._e))

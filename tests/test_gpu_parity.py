@@ -306,3 +306,33 @@ def test_pinned_host_state_round_trip(flic, precision):
     if precision == "fp64":
         for f in FIELDS:
             assert np.array_equal(ref[f], s.state[f]), f
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+def test_cooling_placeholder(flic, precision, tol):
+    """The gas cooling placeholder q = Lambda rho^2 sqrt(eps) (reading s13): two
+    steps of a rough state equal the oracle's; a uniform gas at rest decays like
+    the oracle's (pinned there to the exact solution of its ODE)."""
+    N = 24
+    s = I.random_state((N, N, N), seed=77, rough=True)
+    prm = O.Params(h=s.h, gamma=s.gamma, cooling=0.8)
+    ref, _ = O.run(s.state, prm, 2)
+    with flic.Grid(N, precision=precision, gamma=s.gamma, cooling=0.8, box=(-1.0, -1.0 + N * s.h)) as g:
+        g.set_state(s.state)
+        g.step()
+        g.step()
+        out = g.get_state()
+    err = max_rel(out, ref)
+    assert max(err.values()) <= tol, err
+    from helpers import state_from_primitives
+    one = np.ones((16, 16, 16))
+    P = {"xx": 0.3 * one, "yy": 0.3 * one, "zz": 0.3 * one, "xy": 0 * one, "xz": 0 * one, "yz": 0 * one}
+    st = state_from_primitives(1.3 * one, (0 * one, 0 * one, 0 * one), 0.8 * one, 0.5 * one,
+                               (0 * one, 0 * one, 0 * one), P, 5.0 / 3.0)
+    ref, _ = O.run(st, O.Params(h=2.0 / 16, G=0.0, cooling=0.7), 40, dt=0.01)
+    with flic.Grid(16, precision=precision, G=0.0, cooling=0.7) as g:
+        g.set_state(st)
+        g.run(40, 0.01)
+        out = g.get_state()
+    assert np.max(np.abs(out["e"] - ref["e"])) <= 10 * tol * np.max(ref["e"])
+    assert np.max(ref["e"]) < 0.85 * 1.2   # the gas cooled
