@@ -274,7 +274,20 @@ def make_workload(args, rank):
     raise ValueError(args.config)
 
 
-def roofline_entry(kern, stage_ms, steps, cells, esz, precision, N):
+TRAFFIC_SOURCES = ("paper_1311_0861_gb300/csrc/flic_stencil.cuh", "paper_1311_0861_gb300/csrc/flic_stencil_launch.cuh",
+                   "paper_1311_0861_gb300/csrc/flic_stencil_gas32.cu", "paper_1311_0861_gb300/csrc/flic_stencil_bme32.cu")
+
+
+def traffic_key_hash() -> str:
+    """Hash of the sources that define the float32 fluid kernels and their shapes."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def roofline_entry(kern, stage_ms, steps, cells, esz, precision, N, cand=None):
     avg_s = stage_ms[kern] / steps / 1e3
     alg_bytes = ALG_WORDS[kern] * esz * cells
     peak, peak_kind = peaks()
@@ -282,16 +295,14 @@ def roofline_entry(kern, stage_ms, steps, cells, esz, precision, N):
     r = {"bound": "hbm", "kernel": f"fluid_step_kernel<{'Bme' if kern == 'bme' else 'Gas'}Phys>",
          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
          "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3}
-    # ncu DRAM bytes per launch, recorded for a given kernel source: used only
-    # while the kernel source is unchanged
+    # ncu DRAM bytes per launch, recorded for a given kernel source and launch
+    # shape: used only while the sources are unchanged
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file) and N is not None:
+    if os.path.exists(traffic_file) and N is not None and cand is not None:
         try:
-            import hashlib
             rec = json.load(open(traffic_file))
-            src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest()[:16] == rec["sha256_16"]:
-                r["traffic"] = rec.get(f"{kern}-{precision}-{N}")
+            if rec.get("sha256_16") == traffic_key_hash():
+                r["traffic"] = rec.get(f"{kern}-{precision}-{N}-shape{cand}")
         except Exception:
             pass
     return r
@@ -336,7 +347,8 @@ def run_single(args, rank, world, stream, clocks):
     value = agg["cells"] / agg["max_s"]
     d = g.step_diagnostics()
     kern = max(("gas", "bme"), key=lambda k: stage_ms[k])
-    roofline = roofline_entry(kern, stage_ms, args.steps, N ** 3, esz, args.precision, N)
+    tcfg = g.tile_config()
+    roofline = roofline_entry(kern, stage_ms, args.steps, N ** 3, esz, args.precision, N, cand=tcfg[kern])
 
     # ---- end to end through the public API with pinned host buffers ----
     e2e = None
