@@ -64,3 +64,38 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     rc = lib.flic_state_diagnostics_noalloc(ptrs, None, 2048, 0.01, 5.0 / 3.0, None, ctypes.byref(out))
     assert rc == flic.ERR_INVALID_ARG
     assert b"1024" in lib.flic_last_error(None)
+
+
+NOALLOC_FIRST_CALL = r"""
+import json, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1311_0861_gb300 import flic, inputs as I
+import oracle as O
+N = 16
+s = I.random_state((N, N, N), seed=21)
+dev = [torch.from_numpy(np.ascontiguousarray(s.state[f])).cuda() for f in flic.FIELDS]
+torch.cuda.synchronize()
+d = flic.state_diagnostics_noalloc(dev, None, N, s.h, s.gamma)   # the library's first call in this process
+prm = O.Params(h=s.h, gamma=s.gamma)
+ref = O.diagnostics(s.state, np.zeros((N, N, N)), prm)
+ref["vmax"] = O.max_signal_speed(s.state, prm)
+print(json.dumps({"got": {k: d[k] for k in ref}, "want": ref}))
+"""
+
+
+def test_noalloc_as_the_first_call_in_a_fresh_process(env):
+    """The entry point's set-up (module load, address look-up) on a device where
+    no other call of the library ran first; checked against the oracle's sums."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", NOALLOC_FIRST_CALL, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    for k, want in out["want"].items():
+        got = out["got"][k]
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (k, got, want)
