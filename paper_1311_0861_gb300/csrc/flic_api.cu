@@ -114,6 +114,7 @@ static StencilArgs<T> fluid_args(const flic_handle* h, int fluid, const StepCfg&
     a.tz = c.tz;
     a.tiles_x = c.tiles_x;
     a.tiles_y = c.tiles_y;
+    a.zparts = c.zparts;
     a.partials = fluid == FLUID_GAS ? h->part_gas : h->part_bme;
     return a;
 }
@@ -619,10 +620,14 @@ int flic_tile_config(flic_handle* h, int* gas, int* bme, char* text, int len) {
                                  : stencil_cands<float>(FLUID_GAS, &ng)[h->gcfg.cand].name;
         const char* bn = h->fp64 ? stencil_cands<double>(FLUID_BME, &nb)[h->bcfg.cand].name
                                  : stencil_cands<float>(FLUID_BME, &nb)[h->bcfg.cand].name;
-        char gs[64], bs[64];
-        if (h->gcfg.balanced > 0) snprintf(gs, sizeof gs, "balanced split over %d blocks", h->gcfg.balanced);
+        char gs[96], bs[96];
+        if (h->gcfg.balanced > 0)
+            snprintf(gs, sizeof gs, "balanced split over %d blocks (%d part%s per tile column)", h->gcfg.balanced,
+                     h->gcfg.zparts, h->gcfg.zparts > 1 ? "s" : "");
         else snprintf(gs, sizeof gs, "z chunks of %d planes", h->gcfg.tz);
-        if (h->bcfg.balanced > 0) snprintf(bs, sizeof bs, "balanced split over %d blocks", h->bcfg.balanced);
+        if (h->bcfg.balanced > 0)
+            snprintf(bs, sizeof bs, "balanced split over %d blocks (%d part%s per tile column)", h->bcfg.balanced,
+                     h->bcfg.zparts, h->bcfg.zparts > 1 ? "s" : "");
         else snprintf(bs, sizeof bs, "z chunks of %d planes", h->bcfg.tz);
         snprintf(text, size_t(len), "gas: %s, %s; moments: %s, %s", gn, gs, bn, bs);
     }

@@ -17,6 +17,7 @@ struct StepCfg {
     int tiles_x = 0, tiles_y = 0;
     int tz = 0, blocks_z = 0;   // tz = 0: balanced split over `balanced` blocks
     int balanced = 0;
+    int zparts = 1;       // balanced split: parts per tile column
     int threads = 0;
     size_t smem = 0;
     int num_blocks() const { return balanced > 0 ? balanced : tiles_x * tiles_y * blocks_z; }
@@ -24,8 +25,10 @@ struct StepCfg {
 
 enum Fluid { FLUID_GAS = 0, FLUID_BME = 1 };
 // How a single grid's z planes are split over blocks (a batched ensemble always
-// uses (tile, chunk) work items).
-enum Split { SPLIT_CHUNK = 0, SPLIT_BALANCED = 1 };
+// uses (tile, chunk) work items): a (tile, z chunk) grid; a balanced split over
+// one block per resident slot whose units are tile columns cut into parts when
+// there are fewer tiles than blocks; the same with whole tile columns only.
+enum Split { SPLIT_CHUNK = 0, SPLIT_BALANCED = 1, SPLIT_BALANCED_WHOLE = 2 };
 
 // One compiled launch shape of a fluid kernel (tile, threads, occupancy, staging)
 // together with the z split it is used with on a single grid: an entry of the

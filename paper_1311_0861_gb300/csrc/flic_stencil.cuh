@@ -52,6 +52,7 @@ struct StencilArgs {
     int tz;                   // z planes per block; 0: balanced split (below)
     int tiles_x;              // tiles along x (ceil(n / TX))
     int tiles_y;              // tiles along y (ceil(n / TY))
+    int zparts;               // balanced split: parts each tile column is cut into (n % zparts == 0)
     int outflow;              // hydro boundaries: 0 periodic wrap, 1 zero-gradient ghost cells
     const double* tau;        // step size (device scalar)
     double inv_h;             // 1 / h
@@ -534,15 +535,25 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     const int tid = threadIdx.x;
     // Work of this block: one (tile, z chunk) of a batched work list or of the
     // (tile, chunk) grid; or, with tz = 0, a balanced split over B blocks (one
-    // per resident slot): F = T / B rounds of whole tile columns (block b takes
-    // tiles b, b + B, ...; all blocks march the same planes, so neighbouring
-    // tiles share their halos in L2), then an equal share of the tile-major
-    // (tile, plane) sequence of the remaining T - F B tiles, walked as segments
-    // that each lie in one tile column.
+    // per resident slot).  The work is cut into units -- each tile column in K
+    // equal parts along z (K > 1 only when there are fewer tiles than blocks),
+    // unit v = tile (v mod T) of part (v / T) -- and the blocks take F = K T / B
+    // rounds of whole units (block b takes units b, b + B, ...; concurrent blocks
+    // march the same planes of neighbouring tiles, which share their halos in
+    // L2), then an equal share of the unit-major (unit, plane) sequence of the
+    // remaining K T - F B units, walked as segments that each lie in one unit.
     int tile = 0, prow, z0 = 0, z1 = 0;
     long long u = 0, u_end = 0;   // remainder range, in plane updates
     int round = 0, full_rounds = 0;
+    int ntiles = 1, Lp = 1;       // tiles; planes per unit
     StencilArgs<T> a;
+    // unit v from plane offset off, at most `left` planes
+    auto unit_seg = [&](int v, int off, long long left) {
+        tile = v % ntiles;
+        const int zb = (v / ntiles) * Lp;
+        z0 = zb + off;
+        z1 = (left < Lp - off) ? z0 + int(left) : zb + Lp;
+    };
     if (batch.work) {
         const WorkItem w = batch.work[blockIdx.x];
         a = batch.table[w.run];
@@ -558,21 +569,21 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             z0 = blockIdx.y * a.tz;
             z1 = min(z0 + a.tz, a.n);
         } else {
-            const int ntiles = a.tiles_x * a.tiles_y;
-            full_rounds = ntiles / int(gridDim.x);
-            const long long U = (long long)(ntiles - full_rounds * int(gridDim.x)) * a.n;
+            ntiles = a.tiles_x * a.tiles_y;
+            const int K = a.zparts > 0 ? a.zparts : 1;
+            Lp = a.n / K;
+            const int units = ntiles * K;
+            full_rounds = units / int(gridDim.x);
+            const long long U = (long long)(units - full_rounds * int(gridDim.x)) * Lp;
             u = U * blockIdx.x / gridDim.x;
             u_end = U * (blockIdx.x + 1) / gridDim.x;
             prow = blockIdx.x;
             if (full_rounds > 0) {
-                tile = blockIdx.x;
-                z0 = 0;
-                z1 = a.n;
+                unit_seg(blockIdx.x, 0, Lp);
                 round = 1;
             } else {
-                tile = int(u / a.n);
-                z0 = int(u % a.n);
-                z1 = (u_end - u < a.n - z0) ? z0 + int(u_end - u) : a.n;
+                const int ur = int(u / Lp);
+                unit_seg(ur, int(u - (long long)ur * Lp), u_end - u);
             }
         }
     }
@@ -957,25 +968,19 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         cp_async_wait<0>();
         // next segment (balanced split only)
         if (!balanced) break;
-        if (round > 0 && round < full_rounds) {           // next whole tile column
-            tile = blockIdx.x + round * int(gridDim.x);
-            z0 = 0;
-            z1 = N;
+        if (round > 0 && round < full_rounds) {           // next whole unit
+            unit_seg(blockIdx.x + round * int(gridDim.x), 0, Lp);
             ++round;
         } else {
-            if (round > 0) {                               // whole columns done: the remainder share
+            if (round > 0) {                               // whole units done: the remainder share
                 round = 0;
                 if (u >= u_end) break;
-                const long long rt = u / N;
-                tile = full_rounds * int(gridDim.x) + int(rt);
-                z0 = int(u - rt * N);
-                z1 = (u_end - u < N - z0) ? z0 + int(u_end - u) : N;
+                const int ur = int(u / Lp);
+                unit_seg(full_rounds * int(gridDim.x) + ur, int(u - (long long)ur * Lp), u_end - u);
             } else {                                       // within the remainder share
                 u += z1 - z0;
                 if (u >= u_end) break;
-                ++tile;
-                z0 = 0;
-                z1 = (u_end - u < N) ? int(u_end - u) : N;
+                unit_seg(full_rounds * int(gridDim.x) + int(u / Lp), 0, u_end - u);
             }
         }
         __syncthreads();   // the ring and the coordinate tables are reused

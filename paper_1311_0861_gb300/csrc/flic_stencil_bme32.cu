@@ -24,6 +24,8 @@ const StencilCand<float> kCands[] = {
                       SPLIT_CHUNK),
     FLIC_STENCIL_CAND(P, float, C1, "32x8 tile, 352 threads (one per updated cell), 1 block/SM",
                       SPLIT_BALANCED),
+    FLIC_STENCIL_CAND(P, float, C1, "32x8 tile, 352 threads (one per updated cell), 1 block/SM",
+                      SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, float, C2, "32x16 tile, 608 threads (one per updated cell), 1 block/SM",
                       SPLIT_BALANCED),
     FLIC_STENCIL_CAND(P, float, C3, "16x16 tile, 320 threads (one per updated cell), 1 block/SM",
@@ -35,6 +37,12 @@ const StencilCand<float> kCands[] = {
                       "32x8 tile, 352 threads (one per updated cell), 1 block/SM, one barrier per plane, "
                       "f' as field pairs",
                       SPLIT_BALANCED),
+    FLIC_STENCIL_CAND(P, float, C5,
+                      "32x8 tile, 352 threads (one per updated cell), 1 block/SM, one barrier per plane, "
+                      "f' as field pairs",
+                      SPLIT_BALANCED_WHOLE),
+    FLIC_STENCIL_CAND(P, float, C0, "32x12 tile, 480 threads (one per updated cell), 1 block/SM",
+                      SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, float, C6,
                       "32x12 tile, 480 threads (one per updated cell), 1 block/SM, 5 x/y faces per helper thread",
                       SPLIT_BALANCED),

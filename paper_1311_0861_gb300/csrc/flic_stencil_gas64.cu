@@ -10,6 +10,7 @@ using C1 = TileCfg<32, 4, 3, false, false, 0>;
 const StencilCand<double> kCands[] = {
     FLIC_STENCIL_CAND(P, double, C0, "32x8 tile, 256 threads, 2 blocks/SM", SPLIT_CHUNK),
     FLIC_STENCIL_CAND(P, double, C0, "32x8 tile, 256 threads, 2 blocks/SM", SPLIT_BALANCED),
+    FLIC_STENCIL_CAND(P, double, C0, "32x8 tile, 256 threads, 2 blocks/SM", SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, double, C1, "32x4 tile, 128 threads, 3 blocks/SM", SPLIT_CHUNK),
 };
 }  // namespace

@@ -11,9 +11,11 @@ template <class P, typename T, class C>
 struct StencilOps {
     // Launch geometry.  tz > 0 (batched ensembles): a (tile, z chunk) grid of
     // that chunk height.  tz <= 0 (single grid): SPLIT_BALANCED -- one block per
-    // resident slot (the kernel's occupancy times the SM count), whole tile
-    // columns in lockstep rounds, then an equal share of the remaining (tile,
-    // plane) updates, so no wave is partly empty (at least 8 planes a block);
+    // resident slot (the kernel's occupancy times the SM count), whole units in
+    // lockstep rounds, then an equal share of the remaining (unit, plane)
+    // updates, so no wave is partly empty (at least 8 planes a block); a unit is
+    // a tile column, or with fewer tiles than blocks 1/K of one (K = 2, 4, 8,
+    // at least 16 planes; SPLIT_BALANCED_WHOLE keeps whole columns);
     // SPLIT_CHUNK -- a (tile, chunk) grid whose chunk height minimises
     // waves x (chunk + 4).
     static StepCfg cfg(int N, int tz, int split) {
@@ -33,13 +35,18 @@ struct StencilOps {
             if (per_sm < 1) per_sm = 1;
             const long slots = long(sms) * per_sm;
             const long tiles = long(c.tiles_x) * c.tiles_y;
-            if (split == SPLIT_BALANCED) {
+            if (split == SPLIT_BALANCED || split == SPLIT_BALANCED_WHOLE) {
                 long b = slots;
                 if (b > tiles * N / 8) b = tiles * N / 8;
                 if (b < 1) b = 1;
                 c.tz = 0;
                 c.blocks_z = 1;
                 c.balanced = int(b);
+                // fewer tiles than blocks: cut each tile column into K equal parts
+                // (at least 16 planes) so that whole units still fill a round
+                c.zparts = 1;
+                for (int K = 2; split == SPLIT_BALANCED && K <= 8 && tiles * c.zparts < b; K *= 2)
+                    if (N % K == 0 && N / K >= 16) c.zparts = K;
                 return c;
             }
             long best = -1;
