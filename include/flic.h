@@ -11,7 +11,8 @@
  *             Riemann solution), then the Lagrangian stage (face-flux transport);
  *   Sec. 2.2  Boltzmann-moment Eulerian stage (closed-form face solution of the
  *             6x6 linear system), then the Lagrangian stage;
- *   Sec. 2.4  correctness checks kappa_gas, kappa_bme and the energy balance.
+ *   Sec. 2.4  correctness checks kappa_gas, kappa_bme and the energy balance;
+ *   Sec. 2    an optional analytic stand-in for the gas cooling function q.
  * Every stage runs in hand-written CUDA kernels for sm_103a; there is no CPU
  * fallback.
  *
@@ -76,6 +77,17 @@ enum flic_hydro_bc {
     FLIC_HYDRO_OUTFLOW = 1
 };
 
+/* Transport velocity of the Lagrangian stage (Sec. 2.1, whose printed flux averages
+ * four transverse face velocities in a garbled form).  A: the face's own Eulerian
+ * velocity (default, the fused kernels).  B: the mean of the face velocities of
+ * the same orientation at the face's four transverse diagonal neighbours, the
+ * printed form taken literally (periodic hydro boundaries only; two plain kernels
+ * per fluid, for experiments). */
+enum flic_flux_reading {
+    FLIC_FLUX_A = 0,
+    FLIC_FLUX_B = 1
+};
+
 typedef struct flic_grid_desc {
     int n;               /* cells per axis (cube); N = 2^a 3^b, 8 <= N <= 1024 */
     double box_min;      /* domain [box_min, box_max]^3 */
@@ -91,6 +103,7 @@ typedef struct flic_grid_desc {
                             paper takes from Sutherland & Dopita; here an analytic placeholder
                             q = Lambda rho^2 sqrt(eps), subtracted (times tau, time-n state) from E and e
                             in the Eulerian stage; 0 = adiabatic */
+    int flux_reading;    /* enum flic_flux_reading (0: A); ensembles take A only */
 } flic_grid_desc;
 
 /* Per-step record.  Conserved sums describe the state at the START of the step

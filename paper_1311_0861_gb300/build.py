@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflic.so")
 SOURCES = ["flic_api.cu", "flic_stencil.cu", "flic_stencil_gas32.cu", "flic_stencil_bme32.cu", "flic_stencil_gas64.cu",
-           "flic_stencil_bme64.cu", "flic_fft.cu", "flic_fft_iso.cu", "flic_util.cu", "flic_noalloc.cu",
+           "flic_stencil_bme64.cu", "flic_flux_b.cu", "flic_fft.cu", "flic_fft_iso.cu", "flic_util.cu", "flic_noalloc.cu",
            "flic_ensemble.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -30,7 +30,8 @@ def nvcc() -> str:
 # far from the denormal range; saves the special-case paths of the hardware
 # reciprocal and reciprocal square root)
 EXTRA = {src: ["-ftz=true"] for src in ("flic_stencil_gas32.cu", "flic_stencil_bme32.cu",
-                                         "flic_stencil_gas64.cu", "flic_stencil_bme64.cu")}
+                                         "flic_stencil_gas64.cu", "flic_stencil_bme64.cu",
+                                         "flic_flux_b.cu")}
 
 
 def _compile(src: str) -> tuple[str, str]:

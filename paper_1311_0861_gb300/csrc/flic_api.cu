@@ -41,6 +41,9 @@ struct flic_handle {
     int nb_diag = 0;
     StepCfg gcfg, bcfg;
     int rows_gas = 0, rows_bme = 0;   // partial rows allocated per fluid kernel
+    bool flux_b = false;              // reading B of the transport velocity (flic_flux_b.cu)
+    void* fb_fp = nullptr;            // reading B: f' of both fluids (22 fields)
+    void* fb_w = nullptr;             // reading B: +x/+y/+z face velocities of both fluids (6 fields)
     flic_diag* diag_dev = nullptr;    // [0] last step, [1] current-state diagnostics
     flic_diag* diag_host = nullptr;   // pinned
     double* staging = nullptr;        // one float64 field
@@ -119,6 +122,29 @@ static StencilArgs<T> fluid_args(const flic_handle* h, int fluid, const StepCfg&
     return a;
 }
 
+// Arguments of the reading-B kernels of one fluid (state[cur] -> state[1 - cur]).
+template <typename T>
+static FluxBArgs<T> flux_b_args(const flic_handle* h, int fluid) {
+    FluxBArgs<T> a;
+    const int f0 = fluid == FLUID_GAS ? F_RHO : F_N;
+    a.in = field_ptr<T>(h->state[h->cur], h->fs, f0);
+    a.out = field_ptr<T>(h->state[1 - h->cur], h->fs, f0);
+    a.phi = reinterpret_cast<const T*>(h->phi);
+    a.fp = field_ptr<T>(h->fb_fp, h->fs, f0);
+    a.w = field_ptr<T>(h->fb_w, h->fs, fluid == FLUID_GAS ? 0 : 3);
+    a.fs = h->fs;
+    a.n = h->N;
+    a.tau = h->scal + S_TAU;
+    a.inv_h = 1.0 / h->h;
+    a.gamma = T(h->d.gamma);
+    a.eta = T(h->d.eta);
+    a.cool = fluid == FLUID_GAS ? T(h->d.cooling) : T(0);
+    a.partials = fluid == FLUID_GAS ? h->part_gas : h->part_bme;
+    a.vmax = h->scal + S_VMAX_NEXT;
+    a.status = h->status;
+    return a;
+}
+
 // One full step on the handle's stream; flips the state buffers.  With `ev`
 // (5 events) the stage boundaries are recorded: start, after the Poisson solve,
 // after the gas kernel, after the moment kernel, after the final reduction.
@@ -129,14 +155,23 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
     int rc = enqueue_poisson<T>(h);
     if (rc) return rc;
     if (ev) FLIC_CK(h, cudaEventRecord(ev[1], h->st));
-    const StencilArgs<T> ag = fluid_args<T>(h, FLUID_GAS, h->gcfg);
-    FLIC_CK(h, stencil_launch<T>(FLUID_GAS, ag, h->gcfg, h->st));
-    if (ev) FLIC_CK(h, cudaEventRecord(ev[2], h->st));
-    const StencilArgs<T> ab = fluid_args<T>(h, FLUID_BME, h->bcfg);
-    FLIC_CK(h, stencil_launch<T>(FLUID_BME, ab, h->bcfg, h->st));
-    if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));
-    FLIC_CK(h, step_finalize(h->part_gas, h->gcfg.num_blocks(), h->part_bme, h->bcfg.num_blocks(),
-                             h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
+    if (h->flux_b) {
+        for (int fluid = 0; fluid < 2; ++fluid) {
+            FLIC_CK(h, launch_flux_b<T>(fluid, flux_b_args<T>(h, fluid), FLUX_B_BLOCKS, h->st));
+            if (ev) FLIC_CK(h, cudaEventRecord(ev[2 + fluid], h->st));
+        }
+        FLIC_CK(h, step_finalize(h->part_gas, FLUX_B_BLOCKS, h->part_bme, FLUX_B_BLOCKS, h->h * h->h * h->h,
+                                 h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
+    } else {
+        const StencilArgs<T> ag = fluid_args<T>(h, FLUID_GAS, h->gcfg);
+        FLIC_CK(h, stencil_launch<T>(FLUID_GAS, ag, h->gcfg, h->st));
+        if (ev) FLIC_CK(h, cudaEventRecord(ev[2], h->st));
+        const StencilArgs<T> ab = fluid_args<T>(h, FLUID_BME, h->bcfg);
+        FLIC_CK(h, stencil_launch<T>(FLUID_BME, ab, h->bcfg, h->st));
+        if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));
+        FLIC_CK(h, step_finalize(h->part_gas, h->gcfg.num_blocks(), h->part_bme, h->bcfg.num_blocks(),
+                                 h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
+    }
     if (ev) FLIC_CK(h, cudaEventRecord(ev[4], h->st));
     h->cur = 1 - h->cur;
     return FLIC_OK;
@@ -214,7 +249,7 @@ static void free_all(flic_handle* h) {
         if (h->state[i]) cudaFree(h->state[i]);
     }
     void* bufs[] = {h->phi, h->spec, h->tw, h->asin2, h->gtab, h->scal, h->status, h->part_gas, h->part_bme,
-                    h->part_diag, h->level1, h->diag_dev, h->staging};
+                    h->part_diag, h->level1, h->diag_dev, h->staging, h->fb_fp, h->fb_w};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->diag_host) cudaFreeHost(h->diag_host);
@@ -236,6 +271,8 @@ static int init_impl(flic_handle* h) {
     h->gcfg = stencil_cfg<T>(FLUID_GAS, 0, N, 0);
     h->bcfg = stencil_cfg<T>(FLUID_BME, 0, N, 0);
     // partial rows for the largest grid of any candidate shape (the tuner may switch)
+    // and for the reading-B kernels
+    h->rows_gas = h->rows_bme = FLUX_B_BLOCKS;
     for (int fluid = 0; fluid < 2; ++fluid) {
         int nc = 0;
         stencil_cands<T>(fluid, &nc);
@@ -306,6 +343,10 @@ static int init_impl(flic_handle* h) {
     FLIC_CK(h, cudaMemsetAsync(h->diag_dev, 0, 2 * sizeof(flic_diag), h->st));
     FLIC_CK(h, cudaMallocHost(&h->diag_host, 2 * sizeof(flic_diag)));
     FLIC_CK(h, cudaMalloc(&h->staging, h->cells * sizeof(double)));
+    if (h->flux_b) {
+        FLIC_CK(h, cudaMalloc(&h->fb_fp, F_COUNT * h->fs * sizeof(T)));
+        FLIC_CK(h, cudaMalloc(&h->fb_w, 6 * h->fs * sizeof(T)));
+    }
     FLIC_CK(h, cudaStreamSynchronize(h->st));
     return FLIC_OK;
 }
@@ -422,12 +463,18 @@ int flic_init_grid(const flic_grid_desc* desc, void* stream, flic_handle** out) 
     if (desc->precision != FLIC_FP64 && desc->precision != FLIC_MIXED) { g_init_err = "unknown precision"; return FLIC_ERR_INVALID_ARG; }
     if (desc->poisson_bc != FLIC_PERIODIC && desc->poisson_bc != FLIC_ISOLATED) { g_init_err = "unknown Poisson boundary"; return FLIC_ERR_INVALID_ARG; }
     if (desc->hydro_bc != FLIC_HYDRO_PERIODIC && desc->hydro_bc != FLIC_HYDRO_OUTFLOW) { g_init_err = "unknown hydro boundary"; return FLIC_ERR_INVALID_ARG; }
+    if (desc->flux_reading != FLIC_FLUX_A && desc->flux_reading != FLIC_FLUX_B) { g_init_err = "unknown flux reading"; return FLIC_ERR_INVALID_ARG; }
+    if (desc->flux_reading == FLIC_FLUX_B && desc->hydro_bc != FLIC_HYDRO_PERIODIC) {
+        g_init_err = "flux reading B is built for periodic hydro boundaries only";
+        return FLIC_ERR_INVALID_ARG;
+    }
     flic_handle* h = new flic_handle();
     h->d = *desc;
     h->N = desc->n;
     h->h = (desc->box_max - desc->box_min) / desc->n;
     h->fp64 = desc->precision == FLIC_FP64;
     h->iso = desc->poisson_bc == FLIC_ISOLATED;
+    h->flux_b = desc->flux_reading == FLIC_FLUX_B;
     if (stream) {
         h->st = reinterpret_cast<cudaStream_t>(stream);
     } else {
@@ -549,8 +596,9 @@ int flic_profile(flic_handle* h, int nsteps, double dt, double stage_ms[FLIC_NST
 
 int flic_launches_per_step(flic_handle* h) {
     if (!h) return FLIC_ERR_INVALID_ARG;
-    // step setup, five FFT passes (none without gravity), two fluid kernels, two-level reduction
-    return 1 + (h->d.G != 0.0 ? 5 : 0) + 2 + 2;
+    // step setup, five FFT passes (none without gravity), two fluid kernels (four with
+    // reading B), two-level reduction
+    return 1 + (h->d.G != 0.0 ? 5 : 0) + (h->flux_b ? 4 : 2) + 2;
 }
 
 int flic_solve_poisson(flic_handle* h, double* phi_out) {

@@ -500,7 +500,7 @@ int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, f
         if (d.precision != d0.precision || d.poisson_bc != d0.poisson_bc || d.hydro_bc != d0.hydro_bc ||
             d.gamma != d0.gamma || d.G != d0.G ||
             d.courant != d0.courant || d.eta != d0.eta || d.box_min != d0.box_min || d.box_max != d0.box_max ||
-            d.cooling != d0.cooling) {
+            d.cooling != d0.cooling || d.flux_reading != d0.flux_reading) {
             set_global_error("ensemble runs must share every constant except n");
             return FLIC_ERR_INVALID_ARG;
         }
@@ -513,7 +513,7 @@ int flic_ensemble_create(const flic_grid_desc* descs, int nruns, void* stream, f
         }
     }
     if (!(d0.box_max > d0.box_min) || !(d0.gamma > 1.0) || !(d0.courant > 0.0) || !(d0.G >= 0.0) ||
-        !(d0.cooling >= 0.0) ||
+        !(d0.cooling >= 0.0) || d0.flux_reading != FLIC_FLUX_A ||
         (d0.precision != FLIC_FP64 && d0.precision != FLIC_MIXED) ||
         (d0.poisson_bc != FLIC_PERIODIC && d0.poisson_bc != FLIC_ISOLATED) ||
         (d0.hydro_bc != FLIC_HYDRO_PERIODIC && d0.hydro_bc != FLIC_HYDRO_OUTFLOW)) {

@@ -60,6 +60,29 @@ template <typename T>
 cudaError_t stencil_launch_batch(int fluid, int cand, const StencilArgs<T>* table, const WorkItem* work, int nwork,
                                  bool outflow, bool cool, cudaStream_t st);
 
+// Reading B of the Lagrangian flux (flic_flux_b.cu): arguments of the Eulerian
+// and transport kernels of one fluid (fluid-local field order as StencilArgs;
+// fp: NF fields of f', w: 3 fields of +x/+y/+z face velocities, stride fs).
+template <typename T>
+struct FluxBArgs {
+    const T* in;
+    T* out;
+    const T* phi;
+    T* fp;
+    T* w;
+    size_t fs;
+    int n;
+    const double* tau;
+    double inv_h;
+    T gamma, eta, cool;
+    double* partials;
+    double* vmax;
+    unsigned int* status;
+};
+// Both kernels of one fluid over `blocks` blocks (partial rows 0..blocks-1).
+template <typename T> cudaError_t launch_flux_b(int fluid, const FluxBArgs<T>& a, int blocks, cudaStream_t st);
+constexpr int FLUX_B_BLOCKS = 152 * 4;
+
 // float64 <-> storage precision conversion of one field.
 template <typename T> cudaError_t convert_in(const double* src, T* dst, size_t n, cudaStream_t st);
 const void* mapped_device_view(const void* host_ptr);

@@ -46,7 +46,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("box_min", ctypes.c_double), ("box_max", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("G", ctypes.c_double), ("courant", ctypes.c_double),
                 ("eta", ctypes.c_double), ("precision", ctypes.c_int), ("poisson_bc", ctypes.c_int),
-                ("hydro_bc", ctypes.c_int), ("cooling", ctypes.c_double)]
+                ("hydro_bc", ctypes.c_int), ("cooling", ctypes.c_double), ("flux_reading", ctypes.c_int)]
 
 
 class Diag(ctypes.Structure):
@@ -182,18 +182,21 @@ def state_diagnostics_noalloc(fields, phi, n: int, h: float, gamma: float = 5.0 
 
 class Grid:
     """One N^3 grid of the two-fluid step (a libflic handle).  ``poisson``:
-    "periodic" or "isolated" gravity; ``boundary``: "periodic" or "outflow" hydro."""
+    "periodic" or "isolated" gravity; ``boundary``: "periodic" or "outflow" hydro;
+    ``cooling``: Lambda of the cooling placeholder; ``flux``: reading "A" or "B"
+    of the Lagrangian transport velocity."""
 
     def __init__(self, n: int, *, box=(-1.0, 1.0), gamma=5.0 / 3.0, G=1.0, courant=0.2, eta=1e-3,
                  precision: str = "fp64", poisson: str = "periodic", boundary: str = "periodic",
-                 cooling: float = 0.0, stream: int = 0):
+                 cooling: float = 0.0, flux: str = "A", stream: int = 0):
         self.lib = load()
         self.n = int(n)
         self.h = (box[1] - box[0]) / n
         d = GridDesc(int(n), box[0], box[1], gamma, G, courant, eta,
                      {"fp64": FP64, "mixed": MIXED}[precision],
                      {"periodic": PERIODIC, "isolated": ISOLATED}[poisson],
-                     {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary], float(cooling))
+                     {"periodic": HYDRO_PERIODIC, "outflow": HYDRO_OUTFLOW}[boundary], float(cooling),
+                     {"A": 0, "B": 1}[flux])
         self._h = ctypes.c_void_p()
         rc = self.lib.flic_init_grid(ctypes.byref(d), ctypes.c_void_p(stream or None), ctypes.byref(self._h))
         if rc != OK:

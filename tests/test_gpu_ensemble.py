@@ -94,3 +94,24 @@ def test_ensemble_rejects_mixed_constants(flic):
                                 flic.GridDesc(16, -1, 1, 1.4, 1, 0.2, 1e-3, 0, 0))
     out = ctypes.c_void_p()
     assert lib.flic_ensemble_create(descs, 2, None, ctypes.byref(out)) == flic.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_outflow_and_cooling(flic, precision):
+    """Outflow boundaries with isolated gravity, and the cooling placeholder: every
+    run of the ensemble equals the same run stepped alone."""
+    sizes = [16, 24, 12]
+    sts = _states(sizes, 300)
+    for opts in ({"boundary": "outflow", "poisson": "isolated"}, {"cooling": 0.6}):
+        with flic.Ensemble(sizes, precision=precision, **opts) as ens:
+            for r, s in enumerate(sts):
+                ens.set_state(r, s.state)
+            ens.step(3)
+            outs = [ens.get_state(r) for r in range(len(sizes))]
+        for r, (n, s) in enumerate(zip(sizes, sts)):
+            with flic.Grid(n, precision=precision, **opts) as g:
+                g.set_state(s.state)
+                g.run(3)
+                ref = g.get_state()
+            for f in flic.FIELDS:
+                assert np.array_equal(outs[r][f], ref[f]), (opts, r, f)

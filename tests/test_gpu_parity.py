@@ -336,3 +336,42 @@ def test_cooling_placeholder(flic, precision, tol):
         out = g.get_state()
     assert np.max(np.abs(out["e"] - ref["e"])) <= 10 * tol * np.max(ref["e"])
     assert np.max(ref["e"]) < 0.85 * 1.2   # the gas cooled
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+@pytest.mark.parametrize("N", [12, 24])
+def test_flux_reading_b(flic, precision, tol, N):
+    """Reading B of the Lagrangian transport velocity (the printed 4-term
+    transverse mean, oracle Params.flux = "B") on the CUDA path: one step of a
+    rough state equals the oracle's; it differs from reading A."""
+    s = I.random_state((N, N, N), seed=900 + N, rough=True)
+    prm = O.Params(h=s.h, gamma=s.gamma, flux="B")
+    ref, rrec = O.run(s.state, prm, 1)
+    refA, _ = O.run(s.state, O.Params(h=s.h, gamma=s.gamma), 1)
+    with flic.Grid(N, precision=precision, gamma=s.gamma, flux="B", box=(-1.0, -1.0 + N * s.h)) as g:
+        g.set_state(s.state)
+        g.step()
+        out = g.get_state()
+        d = g.step_diagnostics()
+        assert g.launches_per_step() == 1 + 5 + 4 + 2
+    err = max_rel(out, ref)
+    assert max(err.values()) <= tol, err
+    assert max(max_rel(refA, ref).values()) > 1e-4
+    r = rrec[-1]
+    for k in ("mass_gas", "mass_bme", "kappa_gas", "kappa_bme", "vmax"):
+        assert abs(d[k] - r[k]) <= (1e-11 if precision == "fp64" else 1e-5) * abs(r[k]), (k, d[k], r[k])
+
+
+def test_flux_reading_b_ten_steps_and_limits(flic):
+    s = I.head_on(32)
+    prm = O.Params(h=s.h, gamma=s.gamma, flux="B")
+    ref, _ = O.run(s.state, prm, 10)
+    with flic.Grid(32, precision="fp64", gamma=s.gamma, flux="B") as g:
+        g.set_state(s.state)
+        g.run(10)
+        out = g.get_state()
+    err = rel_l1(out, ref)
+    assert max(err.values()) <= 1e-10, err
+    with pytest.raises(flic.FlicError) as ei:
+        flic.Grid(16, flux="B", boundary="outflow")
+    assert ei.value.code == flic.ERR_INVALID_ARG
