@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(FB_THREADS) euler_b_kernel(FluxBArgs<T> a) {
             T lo[NR], hi[NR];
             load_cell<P, T>(a, nbr(i, j, k, d, -1, N), lo);
             load_cell<P, T>(a, nbr(i, j, k, d, +1, N), hi);
-            P::face(lo, 0, ctr, 0, 1, d, a.gamma, fm[d]);
-            P::face(ctr, 0, hi, 0, 1, d, a.gamma, fpv[d]);
+            P::face(lo, 0, ctr, 0, 1, d, a.gamma, rat, fm[d]);
+            P::face(ctr, 0, hi, 0, 1, d, a.gamma, rat, fpv[d]);
             g[d] = (hi[NR - 1] - lo[NR - 1]) * half_ih;
         }
         T ex[NEX > 0 ? NEX : 1];

@@ -128,9 +128,9 @@ struct GasPhys {
     static __device__ __forceinline__ int extra_field(int) { return 0; }
 
     // Eulerian face solution (Sec. 2.1) between ring cells a (left) and b (right)
-    // along axis d.
+    // along axis d (the stress scale is used by the moment policy only).
     static __device__ __forceinline__ void face(const T* ra, int a, const T* rb, int b, int R2,
-                                                int d, T gamma, T* outv) {
+                                                int d, T gamma, T, T* outv) {
         T rL = ra[0 * R2 + a], rR = rb[0 * R2 + b];
         T vL = ra[(1 + d) * R2 + a] * rcp(rL);
         T vR = rb[(1 + d) * R2 + b] * rcp(rR);
@@ -231,9 +231,11 @@ struct BmePhys {
         return (i == j) ? i : (i + j + 2);   // (0,1)->3, (0,2)->4, (1,2)->5
     }
 
-    // Eulerian face solution (Sec. 2.2), normal d with tangents t1 < t2.
+    // Eulerian face solution (Sec. 2.2), normal d with tangents t1 < t2.  The
+    // stresses Pi*_{.d} are returned multiplied by rs (= tau / h in the step), the
+    // factor they carry in every use by the Eulerian update.
     static __device__ __forceinline__ void face(const T* ra, int a, const T* rb, int b, int R2,
-                                                int d, T, T* outv) {
+                                                int d, T, T rs, T* outv) {
         const int t1 = (d == 0) ? 1 : 0;
         const int t2 = (d == 2) ? 1 : 2;
         T nL = ra[0 * R2 + a], nR = rb[0 * R2 + b];
@@ -258,7 +260,7 @@ struct BmePhys {
         T cu = dPnn * (T(1) - s3) * iA * iz1;   // multiplies b_k in u_t
         T cp = dun * rho * (s3 - T(1)) * iz2;   // multiplies b_k in Pi_nt
         outv[d] = T(0.5) * (unL + unR) + dPnn * iz1;
-        outv[3 + d] = A + dun * Z1;
+        outv[3 + d] = rs * (A + dun * Z1);
         if constexpr (std::is_same<T, float>::value) {
             // the two tangents share every coefficient: one packed instruction
             // per operation on (t1, t2)
@@ -270,7 +272,8 @@ struct BmePhys {
             const float2 m1 = make_float2(-1.0f, -1.0f);
             const float2 ut = __ffma2_rn(b, make_float2(cu, cu),
                                          __ffma2_rn(__ffma2_rn(m1, PR, PL), hiz2, __fmul2_rn(h, __fadd2_rn(uL, uR))));
-            const float2 pt = __ffma2_rn(b, make_float2(cp, cp), __ffma2_rn(__ffma2_rn(m1, uR, uL), hZ2, b));
+            const float2 pt = __fmul2_rn(make_float2(rs, rs),
+                                         __ffma2_rn(b, make_float2(cp, cp), __ffma2_rn(__ffma2_rn(m1, uR, uL), hZ2, b)));
             outv[t1] = ut.x;
             outv[t2] = ut.y;
             outv[3 + t1] = pt.x;
@@ -280,12 +283,14 @@ struct BmePhys {
             T b2 = T(0.5) * (P2L + P2R);
             outv[t1] = T(0.5) * (u1L + u1R) + T(0.5) * (P1L - P1R) * iz2 + b1 * cu;
             outv[t2] = T(0.5) * (u2L + u2R) + T(0.5) * (P2L - P2R) * iz2 + b2 * cu;
-            outv[3 + t1] = b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp;
-            outv[3 + t2] = b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp;
+            outv[3 + t1] = rs * (b1 + T(0.5) * (u1L - u1R) * Z2 + b1 * cp);
+            outv[3 + t2] = rs * (b2 + T(0.5) * (u2L - u2R) * Z2 + b2 * cp);
         }
     }
 
-    // nE: the cell's energy tensor (6 components, read directly from global memory)
+    // nE: the cell's energy tensor (6 components, read directly from global memory).
+    // The face stresses fm/fpv[d][3 + i] arrive multiplied by rat = tau / h, so
+    // each tensor component is one chain of fused multiply-adds.
     static __device__ __forceinline__ void euler(const T* r, int c, int R2, const T fm[3][NFACE],
                                                  const T fpv[3][NFACE], const T g[3], T tau,
                                                  T rat, T, T, const T* nE, T* f1) {
@@ -295,13 +300,14 @@ struct BmePhys {
 #pragma unroll
         for (int k = 0; k < 6; ++k) Pi[k] = r[(R_P + k) * R2 + c];
         f1[0] = n;
-        // momentum: q_i -= r sum_d delta_d Pi*_{id} + tau n dPhi/dx_i
+        // momentum: q_i -= sum_d delta_d (rat Pi*_{id}) + tau n dPhi/dx_i
+        const T tn = tau * n;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            T s = T(0);
+            T acc = q[i] - tn * g[i];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) s += fpv[d][3 + i] - fm[d][3 + i];
-            f1[1 + i] = q[i] - rat * s - tau * n * g[i];
+            for (int d = 0; d < 3; ++d) acc = (acc - fpv[d][3 + i]) + fm[d][3 + i];
+            f1[1 + i] = acc;
         }
         // velocity jumps delta_d u*_i
         T du[3][3];
@@ -309,18 +315,26 @@ struct BmePhys {
         for (int d = 0; d < 3; ++d)
 #pragma unroll
             for (int i = 0; i < 3; ++i) du[d][i] = fpv[d][i] - fm[d][i];
+        T tq[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tq[i] = tau * q[i];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int i = (k < 3) ? k : (k == 5 ? 1 : 0);
             const int j = (k < 3) ? k : (k == 3 ? 1 : 2);
-            T sE = T(0), sP = T(0);
+            // nE_ij -= sum_d delta_d (rat Pi*_{jd} u*_i + rat Pi*_{id} u*_j) + tau (q_i g_j + q_j g_i)
+            T acc = nE[k] - tq[i] * g[j];
+            acc = acc - tq[j] * g[i];
+            T sP = T(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                sE += (fpv[d][3 + j] * fpv[d][i] + fpv[d][3 + i] * fpv[d][j])
-                    - (fm[d][3 + j] * fm[d][i] + fm[d][3 + i] * fm[d][j]);
+                acc = acc - fpv[d][3 + j] * fpv[d][i];
+                acc = acc - fpv[d][3 + i] * fpv[d][j];
+                acc = acc + fm[d][3 + j] * fm[d][i];
+                acc = acc + fm[d][3 + i] * fm[d][j];
                 sP += Pi[tc(j, d)] * du[d][i] + Pi[tc(i, d)] * du[d][j];
             }
-            f1[4 + k] = nE[k] - rat * sE - tau * (q[i] * g[j] + q[j] * g[i]);
+            f1[4 + k] = acc;
             f1[10 + k] = Pi[k] - rat * sP;
         }
     }
@@ -741,14 +755,14 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             if (i < NXF) {
                 const int fx = i % Gm::XFW, jy = i / Gm::XFW;
                 const int a2 = (jy + 1) * W2 + fx;
-                P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, v);
+                P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, rat, v);
 #pragma unroll
                 for (int k = 0; k < NFACE; ++k) xfo[k * NXF + i] = v[k];
             } else {
                 const int j = i - NXF;
                 const int jx = j % W1, fy = j / W1;
                 const int a2 = fy * W2 + jx + 1;
-                P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, v);
+                P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, rat, v);
 #pragma unroll
                 for (int k = 0; k < NFACE; ++k) yfo[k * NYF + j] = v[k];
             }
@@ -802,7 +816,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                     }
                 }
                 T zn[NFACE];
-                P::face(re, c2, rp, c2, R2, 2, gamma, zn);
+                P::face(re, c2, rp, c2, R2, 2, gamma, rat, zn);
                 if (active) {
                     T fm[3][NFACE], fpv[3][NFACE];
 #pragma unroll

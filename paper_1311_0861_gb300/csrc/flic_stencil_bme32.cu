@@ -41,8 +41,6 @@ const StencilCand<float> kCands[] = {
                       "32x8 tile, 352 threads (one per updated cell), 1 block/SM, one barrier per plane, "
                       "f' as field pairs",
                       SPLIT_BALANCED_WHOLE),
-    FLIC_STENCIL_CAND(P, float, C0, "32x12 tile, 480 threads (one per updated cell), 1 block/SM",
-                      SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, float, C6,
                       "32x12 tile, 480 threads (one per updated cell), 1 block/SM, 5 x/y faces per helper thread",
                       SPLIT_BALANCED),
