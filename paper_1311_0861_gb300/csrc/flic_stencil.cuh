@@ -91,6 +91,27 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// The warp's total of an accumulator as float64 (valid on lane 0).  float32
+// pairs are combined lane to lane with the two-sum in float32 arithmetic and
+// converted once: float64 additions run on a unit of this GPU that is far
+// slower than the float32 pipes, and these block reductions at the end of the
+// float32 fluid kernels were their only float64 work (the gas kernel at 256^3
+// took 1.2 % longer with float64 warp sums).
+__device__ __forceinline__ double warp_total(const Acc<double>& a) { return warp_sum(a.s); }
+__device__ __forceinline__ double warp_total(const Acc<float>& a) {
+    float s = a.s, c = a.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        const float t = s + s2;
+        const float bb = t - s;
+        c += c2 + ((s - (t - bb)) + (s2 - bb));
+        s = t;
+    }
+    return (double)s + (double)c;
+}
+
 // Two accumulators advanced together: packed float32 two-sum (one instruction
 // per operation for both), plain adds in float64.
 __device__ __forceinline__ void acc_add2(Acc<double>& qa, Acc<double>& qb, double xa, double xb) {
@@ -188,7 +209,8 @@ struct GasPhys {
         T ir = rcp(f[0]);
         T K = T(0.5) * (f[1] * f[1] + f[2] * f[2] + f[3] * f[3]) * ir;
         T E = f[4], e = f[5];
-        q[7].add(fabs(E - e - K));
+        const T kap = fabs(E - e - K);
+        q[7].add(kap);
         T epsE = E - K;
         if (epsE >= eta * E) e = epsE; else E = e + K;
         f[4] = E;
@@ -196,11 +218,10 @@ struct GasPhys {
         T cs = sqr_root(gamma * (gamma - T(1)) * e * ir);
         T vm = fmax(fabs(f[1]), fmax(fabs(f[2]), fabs(f[3]))) * ir + cs;
         vmax = fmax(vmax, vm);
-        // every output is finite iff their sum is (no overflow at these magnitudes)
-        T sum = T(0);
-#pragma unroll
-        for (int i = 0; i < NF; ++i) sum += f[i];
-        bool ok = (f[0] > T(0)) && (e > T(0)) && finite_val(sum);
+        // kappa takes every output but rho through rho > 0 (1/rho, K), so with rho
+        // finite the outputs are all finite iff kappa is (no overflow at these
+        // magnitudes)
+        bool ok = (f[0] > T(0)) && finite_val(f[0]) && (e > T(0)) && finite_val(kap);
         bad = bad || !ok;
     }
 
@@ -379,10 +400,12 @@ struct BmePhys {
         for (int d = 0; d < 3; ++d)
             vm = fmax(vm, fabs(f[1 + d]) * in + sqr_root(T(3) * f[10 + d] * in));
         vmax = fmax(vmax, vm);
-        T sum = T(0);
-#pragma unroll
-        for (int i = 0; i < NF; ++i) sum += f[i];
-        bool ok = (f[0] > T(0)) && (f[10] > T(0)) && (f[11] > T(0)) && (f[12] > T(0)) && finite_val(sum);
+        // kappa takes every input of the balance (n through 1/n, q through q q^T / n,
+        // nE and Pi directly) and the balance maps finite values to finite values,
+        // so with n finite and positive every output is finite iff kappa is (no
+        // overflow at these magnitudes)
+        bool ok = (f[0] > T(0)) && finite_val(f[0]) && (f[10] > T(0)) && (f[11] > T(0)) && (f[12] > T(0)) &&
+                  finite_val(kap);
         bad = bad || !ok;
     }
 
@@ -441,9 +464,12 @@ struct Geom {
     static constexpr size_t fp_one = size_t(P::NF) * R1;
     static constexpr size_t xf_elems = NBUF * xf_one;
     static constexpr size_t yf_elems = NBUF * yf_one;
-    static constexpr size_t zc_elems = size_t(P::NFACE) * R1;
+    // with one updated cell per thread (NTH >= NU) the z face below a cell and the
+    // potential of the plane below stay in that thread's registers
+    static constexpr bool ZREG = NTH >= NU;
+    static constexpr size_t zc_elems = ZREG ? 0 : size_t(P::NFACE) * R1;
     static constexpr size_t fp_elems = NBUF * fp_one;
-    static constexpr size_t phim_elems = R1;
+    static constexpr size_t phim_elems = ZREG ? 0 : R1;
     // fields read only by the Eulerian update (moment energy tensor), staged
     // over the R1 rows in two slots when SEX
     static constexpr size_t ex_slot = size_t(P::NEX) * H1 * W2;
@@ -520,16 +546,22 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     constexpr int NT = Gm::NT, R2 = Gm::R2, W2 = Gm::W2, H2 = Gm::H2, R1 = Gm::R1, W1 = Gm::W1;
     constexpr int NTH = Gm::NTH, NU = Gm::NU;
     // float32: the transport runs on field pairs with packed arithmetic (PK);
-    // the gas kernel also stores f' as field pairs (float2 per pair of fields,
-    // pair-major), loaded and stored 8 bytes at a time (FP2).  In the moment
-    // kernel the pair layout measured slower (its loads raise register
-    // pressure past the 128-register budget), so it keeps scalar rows.
+    // f' may also be stored as field pairs (float2 per pair of fields,
+    // pair-major), loaded and stored 8 bytes at a time (FP2): the default for the
+    // gas, chosen per launch shape for the moments (their 32 x 12 shape fits it
+    // in 128 registers since the z-face carry moved from shared memory to
+    // registers, and is 2-4 % faster with it).
     constexpr bool PK = std::is_same<T, float>::value && P::NF % 2 == 0;
     constexpr bool FP2 = PK && (C::PAIRS < 0 ? P::NF < 16 : C::PAIRS > 0);
     static_assert(!FP2 || ((Gm::ring_elems + Gm::xf_elems + Gm::yf_elems + Gm::zc_elems) % 2 == 0 &&
                            Gm::fp_one % 2 == 0),
                   "the f' buffers must start on an 8-byte boundary");
     constexpr int NF = P::NF, NR = P::NR, NFACE = P::NFACE, NEX = P::NEX;
+    // float32 x/y face solutions stored as value pairs (one 8-byte shared store
+    // or load per two values)
+    constexpr bool FC2 = std::is_same<T, float>::value && NFACE % 2 == 0;
+    static_assert(!FC2 || (Gm::ring_elems % 2 == 0 && Gm::xf_one % 2 == 0 && Gm::yf_one % 2 == 0),
+                  "the face buffers must start on an 8-byte boundary");
     constexpr int NXF = Gm::H1 * Gm::XFW;
     constexpr int NYF = Gm::YFH * W1;
     constexpr int CH = Gm::CH, CPR = Gm::CPR;
@@ -756,15 +788,27 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 const int fx = i % Gm::XFW, jy = i / Gm::XFW;
                 const int a2 = (jy + 1) * W2 + fx;
                 P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, rat, v);
+                if constexpr (FC2) {
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) xfo[k * NXF + i] = v[k];
+                    for (int k = 0; k < NFACE; k += 2)
+                        reinterpret_cast<float2*>(xfo)[(k / 2) * NXF + i] = make_float2(v[k], v[k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NFACE; ++k) xfo[k * NXF + i] = v[k];
+                }
             } else {
                 const int j = i - NXF;
                 const int jx = j % W1, fy = j / W1;
                 const int a2 = fy * W2 + jx + 1;
                 P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, rat, v);
+                if constexpr (FC2) {
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) yfo[k * NYF + j] = v[k];
+                    for (int k = 0; k < NFACE; k += 2)
+                        reinterpret_cast<float2*>(yfo)[(k / 2) * NYF + j] = make_float2(v[k], v[k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NFACE; ++k) yfo[k * NYF + j] = v[k];
+                }
             }
         };
         // face buffers and f' buffer of plane p (by parity with DB)
@@ -782,6 +826,12 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         };
 
         T Wxm = T(0), Wxp = T(0), Wym = T(0), Wyp = T(0);
+        // z face e-1/2 of the thread's updated cell and Phi of plane e-1 there,
+        // carried from phase 1 of plane e-1 (one updated cell per thread)
+        constexpr bool ZREG = Gm::ZREG;
+        T zreg[ZREG ? NFACE : 1], phreg = T(0);
+#pragma unroll
+        for (int k = 0; k < (ZREG ? NFACE : 1); ++k) zreg[k] = T(0);
 
         // Phase 1 of plane e: the z face e+1/2 and the Eulerian update of plane e
         // over R1 (S2), f' into the plane's buffer; the own tile cell keeps its
@@ -819,19 +869,36 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 P::face(re, c2, rp, c2, R2, 2, gamma, rat, zn);
                 if (active) {
                     T fm[3][NFACE], fpv[3][NFACE];
+                    if constexpr (FC2) {
+                        const float2* x2 = reinterpret_cast<const float2*>(xfe) + jy * Gm::XFW + jx;
+                        const float2* y2 = reinterpret_cast<const float2*>(yfe) + jy * W1 + jx;
+#pragma unroll
+                        for (int k = 0; k < NFACE; k += 2) {
+                            const float2 xm = x2[(k / 2) * NXF], xp = x2[(k / 2) * NXF + 1];
+                            const float2 ym = y2[(k / 2) * NYF], yp = y2[(k / 2) * NYF + W1];
+                            fm[0][k] = xm.x; fm[0][k + 1] = xm.y;
+                            fpv[0][k] = xp.x; fpv[0][k + 1] = xp.y;
+                            fm[1][k] = ym.x; fm[1][k + 1] = ym.y;
+                            fpv[1][k] = yp.x; fpv[1][k + 1] = yp.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < NFACE; ++k) {
+                            fm[0][k] = xfe[k * NXF + jy * Gm::XFW + jx];
+                            fpv[0][k] = xfe[k * NXF + jy * Gm::XFW + jx + 1];
+                            fm[1][k] = yfe[k * NYF + jy * W1 + jx];
+                            fpv[1][k] = yfe[k * NYF + (jy + 1) * W1 + jx];
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < NFACE; ++k) {
-                        fm[0][k] = xfe[k * NXF + jy * Gm::XFW + jx];
-                        fpv[0][k] = xfe[k * NXF + jy * Gm::XFW + jx + 1];
-                        fm[1][k] = yfe[k * NYF + jy * W1 + jx];
-                        fpv[1][k] = yfe[k * NYF + (jy + 1) * W1 + jx];
-                        fm[2][k] = zc[k * R1 + c1];
+                        fm[2][k] = ZREG ? zreg[k] : zc[k * R1 + c1];
                         fpv[2][k] = zn[k];
                     }
                     T g[3];
                     g[0] = (re[P::R_PHI * R2 + c2 + 1] - re[P::R_PHI * R2 + c2 - 1]) * half_ih;
                     g[1] = (re[P::R_PHI * R2 + c2 + W2] - re[P::R_PHI * R2 + c2 - W2]) * half_ih;
-                    g[2] = (rp[P::R_PHI * R2 + c2] - phim[c1]) * half_ih;
+                    g[2] = (rp[P::R_PHI * R2 + c2] - (ZREG ? phreg : phim[c1])) * half_ih;
                     T f1[NF];
                     P::euler(re, c2, R2, fm, fpv, g, tau, rat, gamma, cool, ex, f1);
                     if constexpr (FP2) {
@@ -854,9 +921,15 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                         if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
                     }
                 }
+                if constexpr (ZREG) {
 #pragma unroll
-                for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
-                phim[c1] = re[P::R_PHI * R2 + c2];
+                    for (int k = 0; k < NFACE; ++k) zreg[k] = zn[k];
+                    phreg = re[P::R_PHI * R2 + c2];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NFACE; ++k) zc[k * R1 + c1] = zn[k];
+                    phim[c1] = re[P::R_PHI * R2 + c2];
+                }
             }
         };
 
@@ -1005,10 +1078,10 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     constexpr int NW = NTH / 32;
 #pragma unroll
     for (int k = 0; k < P::NQ; ++k) {
-        double v = warp_sum(q[k].value());
+        const double v = warp_total(q[k]);
         if (lane == 0) red[warp * (P::NQ + 1) + k] = v;
     }
-    double vm = warp_max((double)vmax);
+    const double vm = (double)warp_max(vmax);
     unsigned int badw = __any_sync(0xffffffffu, bad) ? 1u : 0u;
     if (lane == 0) red[warp * (P::NQ + 1) + P::NQ] = vm;
     __syncthreads();

@@ -197,6 +197,27 @@ def test_nonphysical_state_is_reported(flic):
         assert ei.value.code == flic.ERR_NONPHYSICAL
 
 
+@pytest.mark.parametrize("field", ["mx", "qy"])
+def test_step_with_overflow_is_reported(flic, field):
+    # float32 storage: a momentum of 1e30 in one cell squares past the float32
+    # range in the kinetic part of the energy balance (Sec. 2.4: K = |m|^2 / 2 rho,
+    # q q^T / n), so the step's output there is not finite and must be flagged;
+    # the float64 path steps the same state without overflow
+    s = I.random_state((16, 16, 16), seed=9)
+    st = {k: v.copy() for k, v in s.state.items()}
+    st[field][3, 4, 5] = 1e30
+    with flic.Grid(16, precision="mixed", gamma=s.gamma) as g:
+        g.set_state(st)
+        with pytest.raises(flic.FlicError) as ei:
+            g.step()
+        assert ei.value.code == flic.ERR_NONPHYSICAL
+        assert g.step_diagnostics()["nonphysical"]
+    with flic.Grid(16, precision="fp64", gamma=s.gamma) as g:
+        g.set_state(st)
+        g.step()
+        assert not g.step_diagnostics()["nonphysical"]
+
+
 def test_invalid_arguments(flic):
     with pytest.raises(flic.FlicError) as ei:
         flic.Grid(10)
