@@ -866,6 +866,10 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                     }
                 }
                 T zn[NFACE];
+                // conserved sums of the own tile cell at time n (before any shared
+                // store of this phase, so its ring reads are shared with the face and
+                // the update below)
+                if (i < NT && e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
                 P::face(re, c2, rp, c2, R2, 2, gamma, rat, zn);
                 if (active) {
                     T fm[3][NFACE], fpv[3][NFACE];
@@ -918,7 +922,6 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                         Wxp = P::normal_velocity(fpv[0], 0);
                         Wym = P::normal_velocity(fm[1], 1);
                         Wyp = P::normal_velocity(fpv[1], 1);
-                        if (e >= z0 && e < z1 && own_valid) P::accumulate_input(re, c2, R2, q);
                     }
                 }
                 if constexpr (ZREG) {
