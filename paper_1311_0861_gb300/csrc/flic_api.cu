@@ -118,6 +118,7 @@ static StencilArgs<T> fluid_args(const flic_handle* h, int fluid, const StepCfg&
     a.tiles_x = c.tiles_x;
     a.tiles_y = c.tiles_y;
     a.zparts = c.zparts;
+    a.ztop = c.ztop;
     a.partials = fluid == FLUID_GAS ? h->part_gas : h->part_bme;
     return a;
 }
@@ -668,15 +669,18 @@ int flic_tile_config(flic_handle* h, int* gas, int* bme, char* text, int len) {
                                  : stencil_cands<float>(FLUID_GAS, &ng)[h->gcfg.cand].name;
         const char* bn = h->fp64 ? stencil_cands<double>(FLUID_BME, &nb)[h->bcfg.cand].name
                                  : stencil_cands<float>(FLUID_BME, &nb)[h->bcfg.cand].name;
-        char gs[96], bs[96];
-        if (h->gcfg.balanced > 0)
-            snprintf(gs, sizeof gs, "balanced split over %d blocks (%d part%s per tile column)", h->gcfg.balanced,
-                     h->gcfg.zparts, h->gcfg.zparts > 1 ? "s" : "");
-        else snprintf(gs, sizeof gs, "z chunks of %d planes", h->gcfg.tz);
-        if (h->bcfg.balanced > 0)
-            snprintf(bs, sizeof bs, "balanced split over %d blocks (%d part%s per tile column)", h->bcfg.balanced,
-                     h->bcfg.zparts, h->bcfg.zparts > 1 ? "s" : "");
-        else snprintf(bs, sizeof bs, "z chunks of %d planes", h->bcfg.tz);
+        char gs[128], bs[128];
+        auto split_text = [](char* out, size_t n, const StepCfg& c) {
+            if (c.balanced > 0 && c.ztop > 0)
+                snprintf(out, n, "balanced split over %d blocks (planes 0-%d of each tile column in lockstep, "
+                         "the tops shared)", c.balanced, c.ztop - 1);
+            else if (c.balanced > 0)
+                snprintf(out, n, "balanced split over %d blocks (%d part%s per tile column)", c.balanced, c.zparts,
+                         c.zparts > 1 ? "s" : "");
+            else snprintf(out, n, "z chunks of %d planes", c.tz);
+        };
+        split_text(gs, sizeof gs, h->gcfg);
+        split_text(bs, sizeof bs, h->bcfg);
         snprintf(text, size_t(len), "gas: %s, %s; moments: %s, %s", gn, gs, bn, bs);
     }
     return FLIC_OK;

@@ -232,6 +232,7 @@ int ens_build_work(flic_ensemble* e) {
             a.vmax = sc + S_VMAX_NEXT;
             a.status = e->status + r;
             a.zparts = 1;
+            a.ztop = 0;
             StencilArgs<T> g = a, b = a;
             g.in = in + F_RHO * c.fs;
             g.out = out + F_RHO * c.fs;

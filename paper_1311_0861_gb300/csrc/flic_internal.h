@@ -18,6 +18,7 @@ struct StepCfg {
     int tz = 0, blocks_z = 0;   // tz = 0: balanced split over `balanced` blocks
     int balanced = 0;
     int zparts = 1;       // balanced split: parts per tile column
+    int ztop = 0;         // balanced split with tops: height of the lockstep part (0: off)
     int threads = 0;
     size_t smem = 0;
     int num_blocks() const { return balanced > 0 ? balanced : tiles_x * tiles_y * blocks_z; }
@@ -27,8 +28,10 @@ enum Fluid { FLUID_GAS = 0, FLUID_BME = 1 };
 // How a single grid's z planes are split over blocks (a batched ensemble always
 // uses (tile, chunk) work items): a (tile, z chunk) grid; a balanced split over
 // one block per resident slot whose units are tile columns cut into parts when
-// there are fewer tiles than blocks; the same with whole tile columns only.
-enum Split { SPLIT_CHUNK = 0, SPLIT_BALANCED = 1, SPLIT_BALANCED_WHOLE = 2 };
+// there are fewer tiles than blocks; the same with whole tile columns only; with
+// fewer tiles than blocks, one block per tile column marching planes [0, H) in
+// lockstep and the other blocks sharing the tops [H, N) of all columns.
+enum Split { SPLIT_CHUNK = 0, SPLIT_BALANCED = 1, SPLIT_BALANCED_WHOLE = 2, SPLIT_TOPS = 3 };
 
 // One compiled launch shape of a fluid kernel (tile, threads, occupancy, staging)
 // together with the z split it is used with on a single grid: an entry of the

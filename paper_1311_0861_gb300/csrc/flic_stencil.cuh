@@ -53,6 +53,7 @@ struct StencilArgs {
     int tiles_x;              // tiles along x (ceil(n / TX))
     int tiles_y;              // tiles along y (ceil(n / TY))
     int zparts;               // balanced split: parts each tile column is cut into (n % zparts == 0)
+    int ztop;                 // > 0: tops split (fewer tiles than blocks), lockstep height H < n
     int outflow;              // hydro boundaries: 0 periodic wrap, 1 zero-gradient ghost cells
     const double* tau;        // step size (device scalar)
     double inv_h;             // 1 / h
@@ -588,15 +589,19 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     // march the same planes of neighbouring tiles, which share their halos in
     // L2), then an equal share of the unit-major (unit, plane) sequence of the
     // remaining K T - F B units, walked as segments that each lie in one unit.
+    // With ztop = H > 0 (fewer tiles than blocks) block b < T marches tile b over
+    // planes [0, H) -- neighbouring tiles in lockstep -- and the other blocks
+    // take equal shares of the tile-major sequence of the tops [H, n).
     int tile = 0, prow, z0 = 0, z1 = 0;
     long long u = 0, u_end = 0;   // remainder range, in plane updates
     int round = 0, full_rounds = 0;
     int ntiles = 1, Lp = 1;       // tiles; planes per unit
+    int zbase = 0;                // first plane of the units (tops: H)
     StencilArgs<T> a;
     // unit v from plane offset off, at most `left` planes
     auto unit_seg = [&](int v, int off, long long left) {
         tile = v % ntiles;
-        const int zb = (v / ntiles) * Lp;
+        const int zb = zbase + (v / ntiles) * Lp;
         z0 = zb + off;
         z1 = (left < Lp - off) ? z0 + int(left) : zb + Lp;
     };
@@ -614,6 +619,23 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             prow = blockIdx.y * gridDim.x + blockIdx.x;
             z0 = blockIdx.y * a.tz;
             z1 = min(z0 + a.tz, a.n);
+        } else if (a.ztop > 0) {
+            ntiles = a.tiles_x * a.tiles_y;
+            prow = blockIdx.x;
+            if (int(blockIdx.x) < ntiles) {   // lockstep part: one segment, u = u_end = 0
+                tile = blockIdx.x;
+                z0 = 0;
+                z1 = a.ztop;
+            } else {                           // a share of the tops
+                zbase = a.ztop;
+                Lp = a.n - a.ztop;
+                const int nb = int(gridDim.x) - ntiles, j = int(blockIdx.x) - ntiles;
+                const long long U = (long long)ntiles * Lp;
+                u = U * j / nb;
+                u_end = U * (j + 1) / nb;
+                const int ur = int(u / Lp);
+                unit_seg(ur, int(u - (long long)ur * Lp), u_end - u);
+            }
         } else {
             ntiles = a.tiles_x * a.tiles_y;
             const int K = a.zparts > 0 ? a.zparts : 1;

@@ -1,25 +1,29 @@
 // Candidate launch shapes of the float32 gas kernel (Sec. 2.1, 2.4).  Entry 0
 // is the default: 32 x 16 tiles with one thread per updated cell (512 tile + 96
-// border cells, 608 threads; the 96 threads without a tile column take 4 x/y
-// faces each first), one block per SM (95 registers), balanced split over whole
-// tile columns.  Measured at 256^3 (ms per launch): 0.435 default, 0.440 with
-// the columns cut in two, 0.442 with 2 helper faces, 0.456 for the 32 x 12 tile
-// with one thread per tile cell and two blocks per SM.
+// border cells, 608 threads; the 96 threads without a tile column take 2 x/y
+// faces each first), one block per SM (95 registers); with fewer tiles than
+// blocks (128 tiles at 256^3) one block per tile column marches the lower planes
+// in lockstep and the other blocks share the tops.  Measured at 256^3 (ms per
+// launch): 0.424 default, 0.426 over whole tile columns, 0.430 with 4 helper
+// faces, 0.456 for the 32 x 12 tile with one thread per tile cell and two blocks
+// per SM.
 #include "flic_stencil_launch.cuh"
 
 namespace flic {
 namespace {
 using P = GasPhys<float>;
-using C0 = TileCfg<32, 16, 1, false, true, 4>;
-using C1 = TileCfg<32, 16, 1, false, true, 2>;
+using C0 = TileCfg<32, 16, 1, false, true, 2>;
+using C1 = TileCfg<32, 16, 1, false, true, 4>;
 using C2 = TileCfg<32, 12, 2, false, false, 0>;
 using C3 = TileCfg<32, 8, 3, false, false, 0>;
 using C4 = TileCfg<32, 8, 2, false, true, 4>;
 #define FLIC_GAS_32X16 "32x16 tile, 608 threads (one per updated cell), 1 block/SM"
 const StencilCand<float> kCands[] = {
-    FLIC_STENCIL_CAND(P, float, C0, FLIC_GAS_32X16, SPLIT_BALANCED_WHOLE),
-    FLIC_STENCIL_CAND(P, float, C0, FLIC_GAS_32X16, SPLIT_BALANCED),
-    FLIC_STENCIL_CAND(P, float, C1, FLIC_GAS_32X16 ", 2 x/y faces per helper thread", SPLIT_BALANCED_WHOLE),
+    FLIC_STENCIL_CAND(P, float, C0, FLIC_GAS_32X16 ", 2 x/y faces per helper thread", SPLIT_TOPS),
+    FLIC_STENCIL_CAND(P, float, C0, FLIC_GAS_32X16 ", 2 x/y faces per helper thread", SPLIT_BALANCED_WHOLE),
+    FLIC_STENCIL_CAND(P, float, C1, FLIC_GAS_32X16 ", 4 x/y faces per helper thread", SPLIT_TOPS),
+    FLIC_STENCIL_CAND(P, float, C1, FLIC_GAS_32X16 ", 4 x/y faces per helper thread", SPLIT_BALANCED_WHOLE),
+    FLIC_STENCIL_CAND(P, float, C1, FLIC_GAS_32X16 ", 4 x/y faces per helper thread", SPLIT_BALANCED),
     FLIC_STENCIL_CAND(P, float, C2, "32x12 tile, 384 threads, 2 blocks/SM", SPLIT_BALANCED),
     FLIC_STENCIL_CAND(P, float, C2, "32x12 tile, 384 threads, 2 blocks/SM", SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, float, C2, "32x12 tile, 384 threads, 2 blocks/SM", SPLIT_CHUNK),

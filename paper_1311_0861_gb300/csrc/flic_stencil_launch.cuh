@@ -3,6 +3,8 @@
 // Included by the translation units that instantiate the candidate shapes.
 #pragma once
 
+#include <algorithm>
+
 #include "flic_internal.h"
 
 namespace flic {
@@ -16,6 +18,8 @@ struct StencilOps {
     // updates, so no wave is partly empty (at least 8 planes a block); a unit is
     // a tile column, or with fewer tiles than blocks 1/K of one (K = 2, 4, 8,
     // at least 16 planes; SPLIT_BALANCED_WHOLE keeps whole columns);
+    // SPLIT_TOPS -- with fewer tiles than blocks, one block per tile column over
+    // planes [0, H) in lockstep and the remaining blocks sharing the tops;
     // SPLIT_CHUNK -- a (tile, chunk) grid whose chunk height minimises
     // waves x (chunk + 4).
     static StepCfg cfg(int N, int tz, int split) {
@@ -35,7 +39,7 @@ struct StencilOps {
             if (per_sm < 1) per_sm = 1;
             const long slots = long(sms) * per_sm;
             const long tiles = long(c.tiles_x) * c.tiles_y;
-            if (split == SPLIT_BALANCED || split == SPLIT_BALANCED_WHOLE) {
+            if (split == SPLIT_BALANCED || split == SPLIT_BALANCED_WHOLE || split == SPLIT_TOPS) {
                 long b = slots;
                 if (b > tiles * N / 8) b = tiles * N / 8;
                 if (b < 1) b = 1;
@@ -47,6 +51,18 @@ struct StencilOps {
                 c.zparts = 1;
                 for (int K = 2; split == SPLIT_BALANCED && K <= 8 && tiles * c.zparts < b; K *= 2)
                     if (N % K == 0 && N / K >= 16) c.zparts = K;
+                // tops: the height H of the lockstep part that balances its blocks
+                // (H planes + 2 warm-up) against the tops' blocks (their share of
+                // T (N - H) planes, + 2 warm-up planes per segment)
+                if (split == SPLIT_TOPS && tiles < b) {
+                    double best = -1.0;
+                    for (int H = 8; H < N; ++H) {
+                        const double share = double(tiles) * (N - H) / double(b - tiles);
+                        const double segs = share / (N - H) + 1.0;
+                        const double cost = std::max(double(H + 2), share + 2.0 * segs);
+                        if (best < 0.0 || cost < best) { best = cost; c.ztop = H; }
+                    }
+                }
                 return c;
             }
             long best = -1;
