@@ -92,15 +92,13 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-// The warp's total of an accumulator as float64 (valid on lane 0).  float32
-// pairs are combined lane to lane with the two-sum in float32 arithmetic and
-// converted once: float64 additions run on a unit of this GPU that is far
-// slower than the float32 pipes, and these block reductions at the end of the
-// float32 fluid kernels were their only float64 work (the gas kernel at 256^3
-// took 1.2 % longer with float64 warp sums).
-__device__ __forceinline__ double warp_total(const Acc<double>& a) { return warp_sum(a.s); }
-__device__ __forceinline__ double warp_total(const Acc<float>& a) {
-    float s = a.s, c = a.c;
+// The warp's total of float32 two-sum pairs (s, c), as a pair (valid on lane 0):
+// combined lane to lane with the two-sum in float32 arithmetic.  The block
+// reductions at the end of the float32 fluid kernels stay in float32 until one
+// conversion per quantity: float64 arithmetic runs on a unit of this GPU that is
+// far slower than the float32 pipes (float64 warp sums had cost the gas kernel
+// 1.2 % at 256^3, and 5 % at 128^3).
+__device__ __forceinline__ void warp_pair_sum(float& s, float& c) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
@@ -110,7 +108,6 @@ __device__ __forceinline__ double warp_total(const Acc<float>& a) {
         c += c2 + ((s - (t - bb)) + (s2 - bb));
         s = t;
     }
-    return (double)s + (double)c;
 }
 
 // Two accumulators advanced together: packed float32 two-sum (one instruction
@@ -1101,25 +1098,54 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     // ---- block reduction of the conserved sums, kappa and the signal speed ----
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int NW = NTH / 32;
+    const unsigned int badw = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+    if constexpr (std::is_same<T, float>::value) {
+        // float32 pairs per warp into the scratch (as floats), then warp 0
+        // combines them; lane 0 converts each quantity once
+        float* redf = reinterpret_cast<float*>(red);
 #pragma unroll
-    for (int k = 0; k < P::NQ; ++k) {
-        const double v = warp_total(q[k]);
-        if (lane == 0) red[warp * (P::NQ + 1) + k] = v;
-    }
-    const double vm = (double)warp_max(vmax);
-    unsigned int badw = __any_sync(0xffffffffu, bad) ? 1u : 0u;
-    if (lane == 0) red[warp * (P::NQ + 1) + P::NQ] = vm;
-    __syncthreads();
-    if (warp == 0) {
+        for (int k = 0; k < P::NQ; ++k) {
+            float s = q[k].s, c = q[k].c;
+            warp_pair_sum(s, c);
+            if (lane == 0) {
+                redf[2 * (warp * (P::NQ + 1) + k)] = s;
+                redf[2 * (warp * (P::NQ + 1) + k) + 1] = c;
+            }
+        }
+        const float vm = warp_max(vmax);
+        if (lane == 0) redf[2 * (warp * (P::NQ + 1) + P::NQ)] = vm;
+        __syncthreads();
+        if (warp == 0) {
 #pragma unroll
-        for (int k = 0; k < P::NQ + 1; ++k) {
-            double v = (lane < NW) ? red[lane * (P::NQ + 1) + k] : 0.0;
-            if (k < P::NQ) {
-                v = warp_sum(v);
-                if (lane == 0) a.partials[size_t(prow) * Q_COUNT + P::qslot(k)] = v;
-            } else {
-                v = warp_max(v);
-                if (lane == 0) atomic_max_nonneg(a.vmax, v);
+            for (int k = 0; k < P::NQ; ++k) {
+                float s = (lane < NW) ? redf[2 * (lane * (P::NQ + 1) + k)] : 0.0f;
+                float c = (lane < NW) ? redf[2 * (lane * (P::NQ + 1) + k) + 1] : 0.0f;
+                warp_pair_sum(s, c);
+                if (lane == 0) a.partials[size_t(prow) * Q_COUNT + P::qslot(k)] = (double)s + (double)c;
+            }
+            const float v = warp_max((lane < NW) ? redf[2 * (lane * (P::NQ + 1) + P::NQ)] : 0.0f);
+            if (lane == 0) atomic_max_nonneg(a.vmax, (double)v);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < P::NQ; ++k) {
+            const double v = warp_sum(q[k].value());
+            if (lane == 0) red[warp * (P::NQ + 1) + k] = v;
+        }
+        const double vm = warp_max((double)vmax);
+        if (lane == 0) red[warp * (P::NQ + 1) + P::NQ] = vm;
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < P::NQ + 1; ++k) {
+                double v = (lane < NW) ? red[lane * (P::NQ + 1) + k] : 0.0;
+                if (k < P::NQ) {
+                    v = warp_sum(v);
+                    if (lane == 0) a.partials[size_t(prow) * Q_COUNT + P::qslot(k)] = v;
+                } else {
+                    v = warp_max(v);
+                    if (lane == 0) atomic_max_nonneg(a.vmax, v);
+                }
             }
         }
     }
