@@ -32,7 +32,8 @@ const StencilCand<float> kCands[] = {
                       SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, float, C5, FLIC_BME_32X8 ", f' as scalar rows", SPLIT_BALANCED_WHOLE),
     FLIC_STENCIL_CAND(P, float, C6, "16x16 tile, 320 threads (one per updated cell), 1 block/SM, f' as field pairs",
-                      SPLIT_BALANCED),
+                      SPLIT_BALANCED),    FLIC_STENCIL_CAND(P, float, C0, FLIC_BME_32X12 ", f' as field pairs", SPLIT_TOPS),
+    FLIC_STENCIL_CAND(P, float, C4, FLIC_BME_32X8 ", one barrier per plane, f' as field pairs", SPLIT_TOPS),
 };
 #undef FLIC_BME_32X12
 #undef FLIC_BME_32X8
