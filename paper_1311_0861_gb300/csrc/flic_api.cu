@@ -162,7 +162,7 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
             if (ev) FLIC_CK(h, cudaEventRecord(ev[2 + fluid], h->st));
         }
         FLIC_CK(h, step_finalize(h->part_gas, FLUX_B_BLOCKS, h->part_bme, FLUX_B_BLOCKS, h->h * h->h * h->h,
-                                 h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
+                                 h->scal, h->status, h->diag_dev, 1, h->level1, !h->fp64, h->st));
     } else {
         const StencilArgs<T> ag = fluid_args<T>(h, FLUID_GAS, h->gcfg);
         FLIC_CK(h, stencil_launch<T>(FLUID_GAS, ag, h->gcfg, h->st));
@@ -171,7 +171,8 @@ static int enqueue_step(flic_handle* h, double dt, cudaEvent_t* ev = nullptr) {
         FLIC_CK(h, stencil_launch<T>(FLUID_BME, ab, h->bcfg, h->st));
         if (ev) FLIC_CK(h, cudaEventRecord(ev[3], h->st));
         FLIC_CK(h, step_finalize(h->part_gas, h->gcfg.num_blocks(), h->part_bme, h->bcfg.num_blocks(),
-                                 h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->level1, h->st));
+                                 h->h * h->h * h->h, h->scal, h->status, h->diag_dev, 1, h->level1, !h->fp64,
+                                 h->st));
     }
     if (ev) FLIC_CK(h, cudaEventRecord(ev[4], h->st));
     h->cur = 1 - h->cur;
@@ -634,7 +635,7 @@ int flic_diagnostics(flic_handle* h, flic_diag* out) {
                  : enqueue_state_check<float>(h, h->scal + S_VMAX_NEXT);
     if (rc) return rc;
     FLIC_CK(h, step_finalize(h->part_diag, h->nb_diag, nullptr, 0, h->h * h->h * h->h, h->scal, h->status,
-                             h->diag_dev + 1, 0, h->level1, h->st));
+                             h->diag_dev + 1, 0, h->level1, 0, h->st));
     FLIC_CK(h, cudaMemcpyAsync(h->diag_host, h->diag_dev, 2 * sizeof(flic_diag), cudaMemcpyDeviceToHost, h->st));
     FLIC_CK(h, cudaStreamSynchronize(h->st));
     *out = h->diag_host[1];

@@ -122,7 +122,7 @@ int ens_enqueue_step(flic_ensemble* e, double dt, cudaEvent_t* ev = nullptr) {
                                       reinterpret_cast<const StencilArgs<T>*>(e->tab_bme[e->cur]), e->work_bme,
                                       e->nwork_bme, e->d.hydro_bc == FLIC_HYDRO_OUTFLOW, false, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[3], e->st));
-    ENS_CK(e, step_finalize_batch(e->fin_tab, e->nruns, 1, e->st));
+    ENS_CK(e, step_finalize_batch(e->fin_tab, e->nruns, 1, e->fp64 ? 0 : 1, e->st));
     if (ev) ENS_CK(e, cudaEventRecord(ev[4], e->st));
     e->cur = 1 - e->cur;
     return FLIC_OK;
@@ -215,7 +215,8 @@ int ens_build_work(flic_ensemble* e) {
         prep[r] = RunScalars{sc, e->status + r, e->d.courant * c.h};
         fin[r] = FinalizeArgs{e->part_gas + size_t(goff[r]) * Q_COUNT, c.gcfg.num_blocks(),
                               e->part_bme + size_t(boff[r]) * Q_COUNT, c.bcfg.num_blocks(), c.h * c.h * c.h, sc,
-                              e->status + r, e->diag + r, e->level1 + size_t(r) * FINALIZE_ROWS * Q_COUNT};
+                              e->status + r, e->diag + r, e->level1 + size_t(r) * FINALIZE_ROWS * Q_COUNT,
+                              std::is_same<T, float>::value ? 1 : 0};
         for (int p = 0; p < 2; ++p) {
             const T* in = reinterpret_cast<const T*>(c.state[p]) + size_t(s) * c.run_stride;
             T* out = reinterpret_cast<T*>(c.state[1 - p]) + size_t(s) * c.run_stride;

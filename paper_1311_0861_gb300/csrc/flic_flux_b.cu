@@ -36,13 +36,42 @@ __device__ __forceinline__ void load_cell(const FluxBArgs<T>& a, size_t c, T* v)
 }
 
 // block sum of the first `count` accumulators into the partial row of the block
-// (slots from P::qslot, starting at `first`), the maximum signal speed and the
-// validity bit
+// (slots from P::qslot, starting at `first`; float32: (sum, compensation) pairs
+// as in the fused kernels), the maximum signal speed and the validity bit
 template <class P, typename T>
 __device__ void block_finish(const FluxBArgs<T>& a, Acc<T>* q, int first, int count, T vmax, bool bad) {
     __shared__ double red[32][P::NQ + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = FB_THREADS / 32;
+    if constexpr (std::is_same<T, float>::value) {
+        float* redf = reinterpret_cast<float*>(&red[0][0]);
+        for (int k = 0; k < count; ++k) {
+            float s = q[first + k].s, c = q[first + k].c;
+            warp_pair_sum(s, c);
+            if (lane == 0) {
+                redf[2 * (warp * (P::NQ + 1) + k)] = s;
+                redf[2 * (warp * (P::NQ + 1) + k) + 1] = c;
+            }
+        }
+        const float vmw = warp_max(vmax);
+        if (lane == 0) redf[2 * (warp * (P::NQ + 1) + P::NQ)] = vmw;
+        const bool badw = __any_sync(0xffffffffu, bad);
+        __syncthreads();
+        if (warp == 0) {
+            for (int k = 0; k < count; ++k) {
+                float s = lane < NW ? redf[2 * (lane * (P::NQ + 1) + k)] : 0.0f;
+                float c = lane < NW ? redf[2 * (lane * (P::NQ + 1) + k) + 1] : 0.0f;
+                warp_pair_sum(s, c);
+                if (lane == 0)
+                    reinterpret_cast<float2*>(a.partials)[size_t(blockIdx.x) * Q_COUNT + P::qslot(first + k)] =
+                        make_float2(s, c);
+            }
+            const float v = warp_max(lane < NW ? redf[2 * (lane * (P::NQ + 1) + P::NQ)] : 0.0f);
+            if (lane == 0 && v > 0.0f) atomic_max_nonneg(a.vmax, (double)v);
+        }
+        if (badw && lane == 0) atomicOr(a.status, ST_NONPHYSICAL);
+        return;
+    }
     for (int k = 0; k < count; ++k) {
         const double v = warp_sum(q[first + k].value());
         if (lane == 0) red[warp][k] = v;

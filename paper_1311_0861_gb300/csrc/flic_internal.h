@@ -78,7 +78,7 @@ struct FluxBArgs {
     const double* tau;
     double inv_h;
     T gamma, eta, cool;
-    double* partials;
+    double* partials;     // float32: (sum, compensation) float32 pairs in the 8-byte slots
     double* vmax;
     unsigned int* status;
 };
@@ -124,6 +124,8 @@ struct RunScalars {
 cudaError_t step_prep_batch(const RunScalars* runs, int nruns, double dt, cudaStream_t st);
 
 // Arguments of the reduction of one run's partial rows (a: gas, b: moments).
+// Each row holds Q_COUNT 8-byte slots: float64 sums, or (pairs = 1, written by
+// the float32 kernels) float32 (sum, compensation) pairs.
 struct FinalizeArgs {
     const double* pa;
     int na;
@@ -134,16 +136,19 @@ struct FinalizeArgs {
     unsigned int* status;
     flic_diag* diag;
     double* level1;
+    int pairs;
 };
-// one two-level reduction per run of the device table
-cudaError_t step_finalize_batch(const FinalizeArgs* table, int nruns, int count_step, cudaStream_t st);
+// one reduction per run of the device table (all runs of one kind of row)
+cudaError_t step_finalize_batch(const FinalizeArgs* table, int nruns, int count_step, int pairs, cudaStream_t st);
 
 // Sums the per-block partials (fixed order, compensated), writes the record and
 // advances vmax_cur, time and the step counter.  count_step = 0 for a
-// diagnostics-only reduction.  level1: FINALIZE_ROWS x Q_COUNT doubles of scratch.
+// diagnostics-only reduction.  float64 rows: two levels (FINALIZE_ROWS blocks,
+// then one; level1: FINALIZE_ROWS x Q_COUNT doubles of scratch); float32 pair
+// rows: one block in float32 two-sum arithmetic, one conversion per quantity.
 constexpr int FINALIZE_ROWS = 64;
 cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
-                          unsigned int* status, flic_diag* diag, int count_step, double* level1,
+                          unsigned int* status, flic_diag* diag, int count_step, double* level1, int pairs,
                           cudaStream_t st);
 
 }  // namespace flic

@@ -109,7 +109,7 @@ extern "C" int flic_state_diagnostics_noalloc(const double* const fields[FLIC_NF
     NOALLOC_CK(state_reduce<double>(f, phi, cells, gamma, sc->partials, int(rows), sc->scal + S_VMAX_NEXT,
                                     sc->status, st));
     NOALLOC_CK(step_finalize(sc->partials, int(rows), nullptr, 0, h * h * h, sc->scal, sc->status, &sc->diag, 0,
-                             sc->level1, st));
+                             sc->level1, 0, st));
     NOALLOC_CK(cudaMemcpyAsync(out, &sc->diag, sizeof(flic_diag), cudaMemcpyDeviceToHost, st));
     NOALLOC_CK(cudaStreamSynchronize(st));
     out->step = 0;

@@ -59,7 +59,8 @@ struct StencilArgs {
     double inv_h;             // 1 / h
     T gamma, eta;
     T cool;                   // Lambda of the gas cooling placeholder (0: adiabatic)
-    double* partials;         // [num_blocks][Q_COUNT] per-block sums (unscaled by h^3)
+    double* partials;         // [num_blocks][Q_COUNT] per-block sums (unscaled by h^3); float32
+                              // kernels store (sum, compensation) float32 pairs in the 8-byte slots
     double* vmax;             // signal speed of the output state (atomic max)
     unsigned int* status;     // ST_* bits
 };
@@ -1100,8 +1101,8 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     constexpr int NW = NTH / 32;
     const unsigned int badw = __any_sync(0xffffffffu, bad) ? 1u : 0u;
     if constexpr (std::is_same<T, float>::value) {
-        // float32 pairs per warp into the scratch (as floats), then warp 0
-        // combines them; lane 0 converts each quantity once
+        // float32 pairs per warp into the scratch, then warp 0 combines them and
+        // writes the block's partial row as float32 (sum, compensation) pairs
         float* redf = reinterpret_cast<float*>(red);
 #pragma unroll
         for (int k = 0; k < P::NQ; ++k) {
@@ -1121,7 +1122,8 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 float s = (lane < NW) ? redf[2 * (lane * (P::NQ + 1) + k)] : 0.0f;
                 float c = (lane < NW) ? redf[2 * (lane * (P::NQ + 1) + k) + 1] : 0.0f;
                 warp_pair_sum(s, c);
-                if (lane == 0) a.partials[size_t(prow) * Q_COUNT + P::qslot(k)] = (double)s + (double)c;
+                if (lane == 0)
+                    reinterpret_cast<float2*>(a.partials)[size_t(prow) * Q_COUNT + P::qslot(k)] = make_float2(s, c);
             }
             const float v = warp_max((lane < NW) ? redf[2 * (lane * (P::NQ + 1) + P::NQ)] : 0.0f);
             if (lane == 0) atomic_max_nonneg(a.vmax, (double)v);

@@ -269,12 +269,9 @@ __device__ __forceinline__ void finalize_level1_body(const FinalizeArgs& f, int 
     if (threadIdx.x < Q_COUNT) f.level1[size_t(blk) * Q_COUNT + threadIdx.x] = res[threadIdx.x];
 }
 
-__device__ __forceinline__ void finalize_level2_body(const FinalizeArgs& f, int count_step) {
-    __shared__ double res[Q_COUNT];
-    block_sum_rows<64>(f.level1, FIN_BLOCKS, nullptr, 0, 0, FIN_BLOCKS, res);
-    if (threadIdx.x < Q_COUNT) res[threadIdx.x] *= f.h3;
-    __syncthreads();
-    if (threadIdx.x == 0) {
+// The record of the sums res (already scaled by h^3); thread 0 only.
+__device__ __forceinline__ void write_record(const FinalizeArgs& f, const double* res, int count_step) {
+    {
         flic_diag* d = f.diag;
         double* scal = f.scal;
         d->mass_gas = res[Q_MASS_GAS];
@@ -305,11 +302,79 @@ __device__ __forceinline__ void finalize_level2_body(const FinalizeArgs& f, int 
     }
 }
 
+__device__ __forceinline__ void finalize_level2_body(const FinalizeArgs& f, int count_step) {
+    __shared__ double res[Q_COUNT];
+    block_sum_rows<64>(f.level1, FIN_BLOCKS, nullptr, 0, 0, FIN_BLOCKS, res);
+    if (threadIdx.x < Q_COUNT) res[threadIdx.x] *= f.h3;
+    __syncthreads();
+    if (threadIdx.x == 0) write_record(f, res, count_step);
+}
+
+// Rows of float32 (sum, compensation) pairs: each thread folds a fixed set of
+// rows into per-quantity pairs with the two-sum, the warps and then warp 0
+// combine them lane to lane (the same float32 two-sum), and lane k converts
+// quantity k once -- no float64 arithmetic in the reduction itself (the
+// float64 unit of this GPU is far slower than the float32 pipes).
+constexpr int FIN_PAIR_THREADS = 256;
+__device__ __forceinline__ void finalize_pairs_body(const FinalizeArgs& f, int count_step) {
+    constexpr int NW = FIN_PAIR_THREADS / 32;
+    __shared__ float part[NW][Q_COUNT][2];
+    __shared__ double res[Q_COUNT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb = f.pb ? f.nb : 0;
+    const int rows = f.na + nb;
+    float s[Q_COUNT], c[Q_COUNT];
+#pragma unroll
+    for (int k = 0; k < Q_COUNT; ++k) { s[k] = 0.0f; c[k] = 0.0f; }
+    for (int r = threadIdx.x; r < rows; r += FIN_PAIR_THREADS) {
+        const float2* p = reinterpret_cast<const float2*>(r < f.na ? f.pa + size_t(r) * Q_COUNT
+                                                                   : f.pb + size_t(r - f.na) * Q_COUNT);
+#pragma unroll
+        for (int k = 0; k < Q_COUNT; ++k) {
+            const float2 x = p[k];
+            const float t = s[k] + x.x;
+            const float bb = t - s[k];
+            c[k] += x.y + ((s[k] - (t - bb)) + (x.x - bb));
+            s[k] = t;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < Q_COUNT; ++k) {
+        warp_pair_sum(s[k], c[k]);
+        if (lane == 0) {
+            part[warp][k][0] = s[k];
+            part[warp][k][1] = c[k];
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float ms = 0.0f, mc = 0.0f;   // quantity `lane` (lanes < Q_COUNT)
+#pragma unroll
+        for (int k = 0; k < Q_COUNT; ++k) {
+            float ss = lane < NW ? part[lane][k][0] : 0.0f;
+            float cc = lane < NW ? part[lane][k][1] : 0.0f;
+            warp_pair_sum(ss, cc);
+            if (lane == k) { ms = ss; mc = cc; }
+        }
+        if (lane < Q_COUNT) res[lane] = ((double)ms + (double)mc) * f.h3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) write_record(f, res, count_step);
+}
+
 __global__ void __launch_bounds__(256) finalize_level1(FinalizeArgs f) {
     finalize_level1_body(f, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(64) step_finalize_kernel(FinalizeArgs f, int count_step) {
     finalize_level2_body(f, count_step);
+}
+__global__ void __launch_bounds__(FIN_PAIR_THREADS) step_finalize_pairs_kernel(FinalizeArgs f, int count_step) {
+    finalize_pairs_body(f, count_step);
+}
+__global__ void __launch_bounds__(FIN_PAIR_THREADS) step_finalize_pairs_batch_kernel(
+    const FinalizeArgs* __restrict__ table, int count_step) {
+    const FinalizeArgs f = table[blockIdx.x];
+    finalize_pairs_body(f, count_step);
 }
 // batched: one run per grid row (level 1) / per block (level 2)
 __global__ void __launch_bounds__(256) finalize_level1_batch(const FinalizeArgs* __restrict__ table) {
@@ -323,14 +388,23 @@ __global__ void __launch_bounds__(64) step_finalize_batch_kernel(const FinalizeA
 }
 
 cudaError_t step_finalize(const double* pa, int na, const double* pb, int nb, double h3, double* scal,
-                          unsigned int* status, flic_diag* diag, int count_step, double* level1, cudaStream_t st) {
-    FinalizeArgs f{pa, na, pb, nb, h3, scal, status, diag, level1};
+                          unsigned int* status, flic_diag* diag, int count_step, double* level1, int pairs,
+                          cudaStream_t st) {
+    FinalizeArgs f{pa, na, pb, nb, h3, scal, status, diag, level1, pairs};
+    if (pairs) {
+        step_finalize_pairs_kernel<<<1, FIN_PAIR_THREADS, 0, st>>>(f, count_step);
+        return cudaGetLastError();
+    }
     finalize_level1<<<FIN_BLOCKS, 256, 0, st>>>(f);
     step_finalize_kernel<<<1, 64, 0, st>>>(f, count_step);
     return cudaGetLastError();
 }
 
-cudaError_t step_finalize_batch(const FinalizeArgs* table, int nruns, int count_step, cudaStream_t st) {
+cudaError_t step_finalize_batch(const FinalizeArgs* table, int nruns, int count_step, int pairs, cudaStream_t st) {
+    if (pairs) {
+        step_finalize_pairs_batch_kernel<<<nruns, FIN_PAIR_THREADS, 0, st>>>(table, count_step);
+        return cudaGetLastError();
+    }
     finalize_level1_batch<<<dim3(FIN_BLOCKS, nruns), 256, 0, st>>>(table);
     step_finalize_batch_kernel<<<nruns, 64, 0, st>>>(table, count_step);
     return cudaGetLastError();
