@@ -297,20 +297,24 @@ __global__ void __launch_bounds__(FftGeom<T, L>::NTX) fft_x_forward(const T* __r
     }
     __syncthreads();
     StockhamIP<C, false, M, RB, 1, M, false, 1, M, L, NTX, (2 * P <= L) ? 1 : 0>::run(A, tws);
-    const C* Z = A;
-    for (int t = threadIdx.x; t < RB * MH; t += NTX) {
-        const int l = t / MH, k = t % MH;
+    // unpack row by row (modes k = threadIdx.x, + NTX, ... of each row: no
+    // division by the odd mode count per element)
+#pragma unroll
+    for (int l = 0; l < RB; ++l) {
         const int row = row0 + l;
-        if (row >= nrows) continue;
-        C zk = Z[l * M + (k == M ? 0 : k)];
-        C zm = cconj(Z[l * M + (k == 0 ? 0 : M - k)]);
-        C Ek, Ok;
-        Ek.x = T(0.5) * (zk.x + zm.x);
-        Ek.y = T(0.5) * (zk.y + zm.y);
-        Ok.x = T(0.5) * (zk.y - zm.y);     // (zk - zm) / (2 i)
-        Ok.y = -T(0.5) * (zk.x - zm.x);
-        const size_t srow = size_t(row / P) * L + row % P;
-        spec[srow * MH + k] = cadd(Ek, cmul(tws[k], Ok));
+        if (row >= nrows) break;
+        const C* Z = A + l * M;
+        C* dst = spec + (size_t(row / P) * L + row % P) * MH;
+        for (int k = threadIdx.x; k < MH; k += NTX) {
+            C zk = Z[k == M ? 0 : k];
+            C zm = cconj(Z[k == 0 ? 0 : M - k]);
+            C Ek, Ok;
+            Ek.x = T(0.5) * (zk.x + zm.x);
+            Ek.y = T(0.5) * (zk.y + zm.y);
+            Ok.x = T(0.5) * (zk.y - zm.y);     // (zk - zm) / (2 i)
+            Ok.y = -T(0.5) * (zk.x - zm.x);
+            dst[k] = cadd(Ek, cmul(tws[k], Ok));
+        }
     }
 }
 
