@@ -194,8 +194,10 @@ int flic_launches_per_step(flic_handle* h);
  * Each fluid kernel (gas: Sec. 2.1, 2.4; moments: Sec. 2.2, 2.4) is compiled in
  * several launch shapes -- tile of columns, threads per block, blocks per SM --
  * each used with a z split over blocks (a balanced split over one block per
- * resident slot, or z chunks); which is fastest depends on the GPU and the grid
- * size, not on the method.  The shapes compute the same cell updates; only the
+ * resident slot -- whole tile columns, equal parts of them, or, with fewer tiles
+ * than blocks, the lower part of every column in lockstep and the tops shared --
+ * or z chunks); which is fastest depends on the GPU and the grid size, not on
+ * the method.  The shapes compute the same cell updates; only the
  * partial sums of the diagnostics are grouped differently.
  *
  * flic_autotune times every shape of both kernels on the handle's CURRENT state
