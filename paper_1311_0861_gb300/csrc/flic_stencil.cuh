@@ -19,7 +19,7 @@
 // tile column i; with WIDE the block has one thread per cell of the tile and
 // its four 1-cell edge strips (rounded up to whole warps), so the Eulerian
 // update of a plane is one item per thread.  Per plane e (two barriers):
-//   S0  asynchronous 8-byte copies of plane e+2 into a three-slot ring (the
+//   S0  asynchronous 16-byte copies of plane e+2 into a three-slot ring (the
 //       fields the faces need, + Phi), one full iteration ahead of its use;
 //   S2  z-face e+1/2, then the Eulerian update of plane e over R1 (f' to smem);
 //   S3  upwind fluxes of f' for the tile cells; plane e-1 completes (its +z flux
@@ -440,7 +440,13 @@ struct Geom {
     static constexpr int TX = C::TX, TY = C::TY;
     static constexpr bool SEX = C::SEX;
     static constexpr int NT = TX * TY;                               // tile (own) cells
-    static constexpr int W2 = TX + 4, H2 = TY + 4, R2 = W2 * H2;   // tile + 2 halo
+    // The ring holds the tile + 2-cell halo, filled by 16-byte asynchronous
+    // copies of CH elements.  Its rows start XO = CH - 2 columns before the halo
+    // (x0 - CH), so that every copy starts on a 16-byte boundary, and are padded
+    // to whole copies: logical column ix (global x0 - 2 + ix) sits at ix + XO.
+    static constexpr int CH = 16 / sizeof(T);                        // elements per 16-byte copy
+    static constexpr int XO = CH - 2;
+    static constexpr int W2 = (TX + 4 + XO + CH - 1) / CH * CH, H2 = TY + 4, R2 = W2 * H2;
     static constexpr int W1 = TX + 2, H1 = TY + 2, R1 = W1 * H1;   // tile + 1 halo
     // cells updated by the Eulerian stage: the tile and its four edge strips
     // (the corners of the 1-cell border feed no tile cell's flux)
@@ -452,9 +458,8 @@ struct Geom {
     static_assert(NTH <= 1024, "tile too large for one block");
     static constexpr int XFW = TX + 3;                               // x faces per R1 row
     static constexpr int YFH = TY + 3;                               // y-face rows
-    static constexpr int CH = 8 / sizeof(T);                         // elements per 8-byte copy
     static constexpr int CPR = W2 / CH;                              // copies per ring row
-    static_assert(W2 % CH == 0, "ring rows must split into 8-byte copies");
+    static_assert(W2 % CH == 0, "ring rows must split into 16-byte copies");
     static constexpr int NBUF = C::DB ? 2 : 1;                      // copies of f' and the x/y faces
     static_assert(!(C::DB && SEX), "the staged energy tensor has no slot for the one-barrier schedule");
     static constexpr size_t ring_elems = size_t(RING_SLOTS) * P::NR * R2;
@@ -482,18 +487,20 @@ struct Geom {
     static constexpr size_t tab_offset = red_offset + sizeof(double) * 32 * (P::NQ + 1);
     static constexpr size_t smem_bytes = tab_offset + sizeof(int) * (2 * CPR + H2);
 
-    // Alignment of every 8-byte shared-memory access (the asynchronous copies,
-    // float2 field pairs, double partials).  The copies land at ring + slot * NR
-    // * R2 + r * R2 + row * W2 + chunk * CH and exb + (slot * NEX + k) * H1 * W2 +
-    // row * W2 + chunk * CH; all terms are multiples of CH when W2 is, and the
-    // region bases must be too.  Global sources are x0 - 2 + CH * i (x0 a multiple
-    // of TX) plus multiples of N (a multiple of 4) and of the field stride (a
-    // multiple of 64), so TX must be a multiple of CH.
-    static_assert(TX % CH == 0, "tile columns must start on an 8-byte boundary");
-    static_assert((size_t(RING_SLOTS) * P::NR * R2) % CH == 0 && R2 % CH == 0, "ring slots and fields 8-byte aligned");
-    static_assert(!SEX || ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems) * sizeof(T)) % 8 == 0,
-                  "staged energy-tensor rows must start on an 8-byte boundary");
-    static_assert(!SEX || (size_t(Geom::H1) * W2) % CH == 0, "staged energy-tensor fields 8-byte aligned");
+    // Alignment of the 16-byte asynchronous copies (and of the 8-byte float2
+    // field pairs and double partials).  The copies land at ring + slot * NR * R2
+    // + r * R2 + row * W2 + chunk * CH and exb + (slot * NEX + k) * H1 * W2 + row *
+    // W2 + chunk * CH; all terms are multiples of CH when W2 is, and the region
+    // bases must be too.  Global sources are x0 - CH + CH * i (x0 a multiple of
+    // TX) plus multiples of N (a multiple of 4) and of the field stride (a
+    // multiple of 64) from 16-byte aligned field bases, so TX must be a multiple
+    // of CH.
+    static_assert(TX % CH == 0, "tile columns must start on a 16-byte boundary");
+    static_assert(XO + TX + 4 <= W2, "ring rows hold the tile and its halo");
+    static_assert((size_t(RING_SLOTS) * P::NR * R2) % CH == 0 && R2 % CH == 0, "ring slots and fields 16-byte aligned");
+    static_assert(!SEX || ((ring_elems + xf_elems + yf_elems + zc_elems + fp_elems + phim_elems) * sizeof(T)) % 16 == 0,
+                  "staged energy-tensor rows must start on a 16-byte boundary");
+    static_assert(!SEX || (size_t(Geom::H1) * W2) % CH == 0, "staged energy-tensor fields 16-byte aligned");
     static_assert(red_offset % 16 == 0 && tab_offset % 8 == 0, "reduction scratch and tables aligned");
     static_assert(smem_bytes <= 227 * 1024, "shared memory of one block");
 };
@@ -518,11 +525,11 @@ __device__ __forceinline__ void r1_coords(int i, int& jx, int& jy) {
     jy = 1 + h;
 }
 
-// Asynchronous 8-byte global -> shared copy (no register staging) and group
-// bookkeeping.
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+// Asynchronous 16-byte global -> shared copy through L2 only (no register
+// staging, no L1 allocation) and group bookkeeping.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -563,7 +570,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                   "the face buffers must start on an 8-byte boundary");
     constexpr int NXF = Gm::H1 * Gm::XFW;
     constexpr int NYF = Gm::YFH * W1;
-    constexpr int CH = Gm::CH, CPR = Gm::CPR;
+    constexpr int CH = Gm::CH, CPR = Gm::CPR, XO = Gm::XO;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);
     T* xf = ring + Gm::ring_elems;
@@ -573,7 +580,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
     T* phim = fpb + Gm::fp_elems;
     T* exb = phim + Gm::phim_elems;
     double* red = reinterpret_cast<double*>(smem_raw + Gm::red_offset);
-    int* xoff = reinterpret_cast<int*>(smem_raw + Gm::tab_offset);   // wrapped x of each 8-byte column chunk
+    int* xoff = reinterpret_cast<int*>(smem_raw + Gm::tab_offset);   // wrapped x of each 16-byte column chunk
     int* yoff = xoff + CPR;                                            // wrapped y * N of R2 rows
     int* xlast = yoff + H2;   // outflow: x of the last element of each chunk (ghost chunks repeat the edge)
 
@@ -679,17 +686,17 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         const int x0 = (tile % a.tiles_x) * TX;
         const int y0 = (tile / a.tiles_x) * TY;
 
-        // x0 - 2 and N are multiples of CH, so no chunk straddles the periodic wrap
+        // x0 - 2 - XO = x0 - CH and N are multiples of CH, so no chunk straddles the periodic wrap
         // or the domain edge: with outflow a chunk lies inside the grid or wholly
         // in the ghost layers (all its elements then copy one edge cell)
         if constexpr (OUT) {
             for (int i = tid; i < CPR; i += NTH) {
-                xoff[i] = min(max(x0 - 2 + CH * i, 0), N - 1);
-                xlast[i] = min(max(x0 - 2 + CH * i + CH - 1, 0), N - 1);
+                xoff[i] = min(max(x0 - 2 - XO + CH * i, 0), N - 1);
+                xlast[i] = min(max(x0 - 2 - XO + CH * i + CH - 1, 0), N - 1);
             }
             for (int i = tid; i < H2; i += NTH) yoff[i] = min(max(y0 + i - 2, 0), N - 1) * N;
         } else {
-            for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 + CH * i, N);
+            for (int i = tid; i < CPR; i += NTH) xoff[i] = wrap_mod(x0 - 2 - XO + CH * i, N);
             for (int i = tid; i < H2; i += NTH) yoff[i] = wrap_mod(y0 + i - 2, N) * N;
         }
         __syncthreads();
@@ -700,7 +707,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
         const bool own_valid = own_tile && (x0 + own_tx < N) && (y0 + own_ty < N);
         const int own_c1 = (own_ty + 1) * W1 + (own_tx + 1);
 
-        // S0 of plane pz: asynchronous 8-byte copies of the ring fields of the plane
+        // S0 of plane pz: asynchronous 16-byte copies of the ring fields of the plane
         // (tile + 2-cell halo) into its ring slot, committed as one group.  Each
         // thread owns fixed (row, chunk) positions and walks the fields.
         constexpr int NPOS = H2 * CPR;
@@ -733,8 +740,8 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                     continue;
                 }
 #pragma unroll
-                for (int r = 0; r < NR - 1; ++r) cp_async8(d + r * R2, src + size_t(P::ring_field(r)) * a.fs);
-                cp_async8(d + (NR - 1) * R2, a.phi + goff);
+                for (int r = 0; r < NR - 1; ++r) cp_async16(d + r * R2, src + size_t(P::ring_field(r)) * a.fs);
+                cp_async16(d + (NR - 1) * R2, a.phi + goff);
             }
             cp_async_commit();
         };
@@ -759,13 +766,14 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 }
 #pragma unroll
                 for (int k = 0; k < NEX; ++k)
-                    cp_async8(d + k * Gm::H1 * W2, src + size_t(P::extra_field(k)) * a.fs);
+                    cp_async16(d + k * Gm::H1 * W2, src + size_t(P::extra_field(k)) * a.fs);
             }
         };
-        // global x of R2 column ix (chunks never straddle the wrap or the edge)
+        // global x of logical R2 column ix (chunks never straddle the wrap or the edge)
         auto gx = [&](int ix) {
-            if constexpr (OUT) return ghost_chunk(ix / CH) ? xoff[ix / CH] : xoff[ix / CH] + ix % CH;
-            return xoff[ix / CH] + ix % CH;
+            const int px = ix + XO;
+            if constexpr (OUT) return ghost_chunk(px / CH) ? xoff[px / CH] : xoff[px / CH] + px % CH;
+            return xoff[px / CH] + px % CH;
         };
 
         const size_t own_g = size_t(yoff[own_ty + 2]) + gx(own_tx + 2);
@@ -806,7 +814,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             T v[NFACE];
             if (i < NXF) {
                 const int fx = i % Gm::XFW, jy = i / Gm::XFW;
-                const int a2 = (jy + 1) * W2 + fx;
+                const int a2 = (jy + 1) * W2 + fx + XO;
                 P::face(rpe, a2, rpe, a2 + 1, R2, 0, gamma, rat, v);
                 if constexpr (FC2) {
 #pragma unroll
@@ -819,7 +827,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
             } else {
                 const int j = i - NXF;
                 const int jx = j % W1, fy = j / W1;
-                const int a2 = fy * W2 + jx + 1;
+                const int a2 = fy * W2 + jx + 1 + XO;
                 P::face(rpe, a2, rpe, a2 + W2, R2, 1, gamma, rat, v);
                 if constexpr (FC2) {
 #pragma unroll
@@ -868,7 +876,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                 int jx, jy;
                 r1_coords<TX, TY>(i, jx, jy);
                 const int c1 = jy * W1 + jx;
-                const int c2 = (jy + 1) * W2 + jx + 1;
+                const int c2 = (jy + 1) * W2 + jx + 1 + XO;
                 T ex[NEX > 0 ? NEX : 1];
                 if (active) {
                     if constexpr (PREF) {
@@ -876,7 +884,7 @@ fluid_step_kernel(StencilArgs<T> a1, BatchArgs<T> batch) {
                         for (int k = 0; k < NEX; ++k) ex[k] = exn[k];
                         if (e + 1 <= z1) load_ex(e + 1);
                     } else if (SEX) {
-                        const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1;
+                        const T* eb = exb + (e & 1) * Gm::ex_slot + jy * W2 + jx + 1 + XO;
 #pragma unroll
                         for (int k = 0; k < NEX; ++k) ex[k] = eb[k * Gm::H1 * W2];
                     } else {
