@@ -599,8 +599,8 @@ int flic_profile(flic_handle* h, int nsteps, double dt, double stage_ms[FLIC_NST
 int flic_launches_per_step(flic_handle* h) {
     if (!h) return FLIC_ERR_INVALID_ARG;
     // step setup, five FFT passes (none without gravity), two fluid kernels (four with
-    // reading B), two-level reduction
-    return 1 + (h->d.G != 0.0 ? 5 : 0) + (h->flux_b ? 4 : 2) + 2;
+    // reading B), the reduction (one launch over float32 pairs; two levels in float64)
+    return 1 + (h->d.G != 0.0 ? 5 : 0) + (h->flux_b ? 4 : 2) + (h->fp64 ? 2 : 1);
 }
 
 int flic_solve_poisson(flic_handle* h, double* phi_out) {

@@ -635,8 +635,9 @@ int flic_ensemble_profile(flic_ensemble* e, int nsteps, double dt, double stage_
 
 int flic_ensemble_launches_per_step(flic_ensemble* e) {
     if (!e) return FLIC_ERR_INVALID_ARG;
-    // setup, five FFT passes per size class, two fluid launches, two-level reduction
-    return 1 + (e->d.G != 0.0 ? 5 * int(e->classes.size()) : 0) + 2 + 2;
+    // setup, five FFT passes per size class, two fluid launches, the reduction (one
+    // launch over float32 pairs; two levels in float64)
+    return 1 + (e->d.G != 0.0 ? 5 * int(e->classes.size()) : 0) + 2 + (e->fp64 ? 2 : 1);
 }
 
 int flic_ensemble_autotune(flic_ensemble* e, int reps, double* ms) {
