@@ -203,7 +203,9 @@ int flic_launches_per_step(flic_handle* h);
  * flic_autotune times every shape of both kernels on the handle's CURRENT state
  * (call it after flic_set_state): one untimed launch, then `reps` launches
  * between two CUDA events on the handle's stream, and keeps the fastest shape of
- * each kernel.  The launches write only the library's spare state buffer: the
+ * each kernel (shapes are taken in index order, and a later one replaces the one
+ * kept only when it is more than 0.5 % faster, so that shapes timing the same
+ * within noise resolve to the lower index).  The launches write only the library's spare state buffer: the
  * current state, time, step count and CFL signal speed are unchanged.  With
  * use_cache != 0 a choice made earlier in this process for the same device model,
  * n, precision and hydro boundary is applied without timing (return value 1);

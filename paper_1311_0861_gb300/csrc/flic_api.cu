@@ -439,7 +439,7 @@ static int tune_impl(flic_handle* h, int reps, double* ms) {
                 }
             }
             if (ms) ms[k] = t;
-            if (t >= 0.0 && (best_ms < 0.0 || t < best_ms)) {
+            if (t >= 0.0 && (best_ms < 0.0 || t < best_ms * (1.0 - TUNE_MARGIN))) {
                 best_ms = t;
                 best[fluid] = c;
             }

@@ -423,7 +423,7 @@ int ens_tune(flic_ensemble* e, int reps, double* ms) {
                     break;
                 }
                 if (ms) ms[k] = tm;
-                if (tm >= 0.0 && (best_ms < 0.0 || tm < best_ms)) {
+                if (tm >= 0.0 && (best_ms < 0.0 || tm < best_ms * (1.0 - TUNE_MARGIN))) {
                     best_ms = tm;
                     best_c[fluid] = c;
                     best_t[fluid] = ENS_TZ_OPTIONS[t];

@@ -25,6 +25,10 @@ struct StepCfg {
 };
 
 enum Fluid { FLUID_GAS = 0, FLUID_BME = 1 };
+// The tuners keep an earlier (lower-index) candidate unless a later one is faster
+// by more than this fraction: shapes that launch identically or time the same
+// within noise resolve to the same, reproducible choice (entry 0 the default).
+constexpr double TUNE_MARGIN = 0.005;
 // How a single grid's z planes are split over blocks (a batched ensemble always
 // uses (tile, chunk) work items): a (tile, z chunk) grid; a balanced split over
 // one block per resident slot whose units are tile columns cut into parts when

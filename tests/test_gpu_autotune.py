@@ -6,7 +6,8 @@ per SM) used with a z split; all must compute the step of Sec. 2.1-2.4:
     of each field's max (N = 24: one ragged tile column; N = 48: several tiles
     with ragged edges for every tile width and height);
   * every shape, float32: equals the oracle to 2e-5 of each field's max;
-  * the tuner's choice is the fastest shape it timed, a second call reuses the
+  * the tuner's choice is the fastest shape it timed (a later shape replacing an
+    earlier one only when more than 0.5 % faster), a second call reuses the
     cached choice, and the tuned step (also as a CUDA-graph replay) equals the
     oracle;
   * ensembles: every (shape, chunk cap) keeps each run equal to the run stepped
@@ -39,6 +40,14 @@ def flic():
 
 def max_rel(a, b):
     return {f: float(np.max(np.abs(a[f] - b[f])) / max(1e-300, np.max(np.abs(b[f])))) for f in FIELDS}
+
+
+def tuned_choice(ms):
+    best, best_ms = 0, -1.0
+    for i, m in enumerate(ms):
+        if m >= 0.0 and (best_ms < 0.0 or m < best_ms * (1.0 - 0.005)):
+            best, best_ms = i, m
+    return best
 
 
 def shape_counts(F, precision):
@@ -79,9 +88,12 @@ def test_autotune_choice_cache_and_parity(flic, precision):
         ng, nb = g.num_tile_configs()
         assert not t["cached"] and len(t["ms_gas"]) == ng and len(t["ms_bme"]) == nb
         cfg = g.tile_config()
-        timed_g = [(m, i) for i, m in enumerate(t["ms_gas"]) if m >= 0]
-        timed_b = [(m, i) for i, m in enumerate(t["ms_bme"]) if m >= 0]
-        assert cfg["gas"] == min(timed_g)[1] and cfg["bme"] == min(timed_b)[1]
+        # in index order, a later shape replaces the kept one only when more than
+        # 0.5 % faster (the same double arithmetic as the library's choice)
+        assert cfg["gas"] == tuned_choice(t["ms_gas"]) and cfg["bme"] == tuned_choice(t["ms_bme"])
+        best_g = min(m for m in t["ms_gas"] if m >= 0)
+        best_b = min(m for m in t["ms_bme"] if m >= 0)
+        assert t["ms_gas"][cfg["gas"]] <= best_g / (1.0 - 0.005) and t["ms_bme"][cfg["bme"]] <= best_b / (1.0 - 0.005)
         assert cfg["text"].startswith("gas: ")
         # tuning leaves the state untouched; the tuned steps (graph replay) match the oracle
         g.run(3)
